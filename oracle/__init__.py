@@ -1,0 +1,225 @@
+"""FP64 CPU oracle of the MP-PIC parcel-grid coupling step (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The product path (the CUDA library and its
+Python binding) never does, and the two share no code: this wrapper has its own
+config struct and its own build of ``mppic_oracle.cpp``.
+
+What each function computes is stated, with the passage of Woo et al.
+(arXiv 2211.15605) it follows, in ``mppic_oracle.cpp``.
+
+Functions without an independent pin: none. The pins live in
+``tests/test_oracle_pins.py`` (closed forms, invariants, brute force).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mppic_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "libmppic_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (FMA contraction off: binning is the plain IEEE product)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrcConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("reserved0", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("rho_g", ctypes.c_double), ("mu_g", ctypes.c_double),
+                ("g", ctypes.c_double * 3), ("gradp", ctypes.c_double * 3),
+                ("rho_p", ctypes.c_double), ("Ps", ctypes.c_double), ("beta", ctypes.c_double),
+                ("eps_cp", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("eps_g_min", ctypes.c_double), ("e_wall", ctypes.c_double),
+                ("drag_mult", ctypes.c_double), ("dscale", ctypes.c_double),
+                ("u_in", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+def make_config(p: dict) -> OrcConfig:
+    c = OrcConfig()
+    for name, _ in OrcConfig._fields_:
+        if name == "reserved0":
+            continue
+        v = p[name]
+        if name in ("g", "gradp"):
+            getattr(c, name)[:] = [float(t) for t in v]
+        elif name in ("nx", "ny", "nz"):
+            setattr(c, name, int(v))
+        else:
+            setattr(c, name, float(v))
+    return c
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            cp = ctypes.POINTER(OrcConfig)
+            L.orc_bin.argtypes = [cp, ctypes.c_long, dp, dp, dp, ip, dp, dp, dp]
+            L.orc_deposit_volume.argtypes = [cp, ctypes.c_long, dp, dp, dp, dp, dp, dp]
+            L.orc_node_fields.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+            L.orc_interp.argtypes = [cp, ctypes.c_long] + [dp] * 11 + [dp]
+            L.orc_drag.argtypes = [cp, ctypes.c_long] + [dp] * 9
+            L.orc_step.argtypes = ([cp, ctypes.c_long] + [dp] * 8 + [ip] + [dp] * 6
+                                   + [ctypes.c_int] + [dp] * 6)
+            L.orc_step.restype = ctypes.c_int
+            L.orc_step_tangent.argtypes = ([cp, ctypes.c_long] + [dp] * 8 + [dp] * 6
+                                           + [ctypes.c_int, dp])
+            L.orc_step_tangent.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def grid_shape(p: dict):
+    return int(p["nx"]), int(p["ny"]), int(p["nz"])
+
+
+def nnode(p: dict) -> int:
+    nx, ny, nz = grid_shape(p)
+    return (nx + 1) * (ny + 1) * (nz + 1)
+
+
+def bin(p, x, y, z):
+    """Cell id and in-cell coordinates (xi, eta, zeta) of each parcel."""
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    n = x.size
+    cell = np.empty(n, np.int32)
+    xi, eta, zeta = np.empty(n), np.empty(n), np.empty(n)
+    c = make_config(p)
+    lib().orc_bin(ctypes.byref(c), n, _d(x), _d(y), _d(z),
+                  cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(xi), _d(eta), _d(zeta))
+    return cell, xi, eta, zeta
+
+
+def deposit_volume(p, x, y, z, d, omega):
+    """Deposited solids volume Vs at every node."""
+    x, y, z, d, omega = map(_f64, (x, y, z, d, omega))
+    Vs = np.empty(nnode(p))
+    c = make_config(p)
+    lib().orc_deposit_volume(ctypes.byref(c), x.size, _d(x), _d(y), _d(z), _d(d), _d(omega),
+                             _d(Vs))
+    return Vs
+
+
+def node_fields(p, Vs, U=(None, None, None)):
+    """(eps_s, ug[3], tau) at nodes from a deposited volume."""
+    Vs = _f64(Vs)
+    U = [_f64(a) for a in U]
+    nn = nnode(p)
+    es, ux, uy, uz, tau = (np.empty(nn) for _ in range(5))
+    c = make_config(p)
+    lib().orc_node_fields(ctypes.byref(c), _d(Vs), _d(U[0]), _d(U[1]), _d(U[2]), _d(es),
+                          _d(ux), _d(uy), _d(uz), _d(tau))
+    return es, np.stack([ux, uy, uz]), tau
+
+
+def interp(p, x, y, z, eps_s, ug, tau, gradp=None):
+    """Interpolated (eps_s, ug[3], gradp[3], gradtau[3]) as a (10, np) array."""
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    es, tau = _f64(eps_s), _f64(tau)
+    ugs = [_f64(ug[a]) for a in range(3)]
+    gps = [None] * 3 if gradp is None else [_f64(gradp[a]) for a in range(3)]
+    out = np.empty((10, x.size))
+    c = make_config(p)
+    lib().orc_interp(ctypes.byref(c), x.size, _d(x), _d(y), _d(z), _d(es), _d(ugs[0]),
+                     _d(ugs[1]), _d(ugs[2]), _d(gps[0]), _d(gps[1]), _d(gps[2]), _d(tau),
+                     _d(out))
+    return out
+
+
+def drag(p, d, eps_s_p, ug_p, u, v, w):
+    """Wen-Yu acceleration coefficient D_p per parcel."""
+    d, es = _f64(d), _f64(eps_s_p)
+    ug = [_f64(ug_p[a]) for a in range(3)]
+    u, v, w = _f64(u), _f64(v), _f64(w)
+    D = np.empty(d.size)
+    c = make_config(p)
+    lib().orc_drag(ctypes.byref(c), d.size, _d(d), _d(es), _d(ug[0]), _d(ug[1]), _d(ug[2]),
+                   _d(u), _d(v), _d(w), _d(D))
+    return D
+
+
+def step(p, state: dict, nsteps: int, U=(None, None, None), gradp=None, outputs=True):
+    """Advance ``nsteps`` coupling steps on a copy of ``state``.
+
+    ``state`` holds x, y, z, u, v, w, d, omega arrays. Returns
+    (new_state, extras, status) where extras has 'cell', 'obj' (nsteps, 2) and,
+    if ``outputs``, the last step's node arrays 'Vs', 'A', 'B' (3, Nn).
+    """
+    s = {k: np.array(state[k], dtype=np.float64, copy=True) for k in
+         ("x", "y", "z", "u", "v", "w")}
+    d, om = _f64(state["d"]), _f64(state["omega"])
+    n = s["x"].size
+    nn = nnode(p)
+    cell = np.empty(n, np.int32)
+    obj = np.empty((max(nsteps, 1), 2))
+    Vs = A = None
+    B = None
+    if outputs:
+        Vs, A, B = np.empty(nn), np.empty(nn), np.empty((3, nn))
+    U = [_f64(a) for a in U]
+    gps = [None] * 3 if gradp is None else [_f64(gradp[a]) for a in range(3)]
+    c = make_config(p)
+    st = lib().orc_step(ctypes.byref(c), n, _d(s["x"]), _d(s["y"]), _d(s["z"]), _d(s["u"]),
+                        _d(s["v"]), _d(s["w"]), _d(d), _d(om),
+                        cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        _d(U[0]), _d(U[1]), _d(U[2]), _d(gps[0]), _d(gps[1]), _d(gps[2]),
+                        int(nsteps), _d(Vs), _d(A),
+                        _d(B[0]) if B is not None else None,
+                        _d(B[1]) if B is not None else None,
+                        _d(B[2]) if B is not None else None, _d(obj))
+    s["d"], s["omega"] = d.copy(), om.copy()
+    extras = {"cell": cell, "obj": obj[:nsteps]}
+    if outputs:
+        extras.update(Vs=Vs, A=A, B=B)
+    return s, extras, int(st)
+
+
+def step_tangent(p, state: dict, nsteps: int, U=(None, None, None), gradp=None):
+    """Forward-mode oracle gradient over ``nsteps`` steps.
+
+    Returns (means, grads, status): means = (<dP>, <H>), grads is a (2, 3) array
+    d(<dP>, <H>)/d(drag_mult, dscale, u_in).
+    """
+    s = {k: np.array(state[k], dtype=np.float64, copy=True) for k in
+         ("x", "y", "z", "u", "v", "w")}
+    d, om = _f64(state["d"]), _f64(state["omega"])
+    U = [_f64(a) for a in U]
+    gps = [None] * 3 if gradp is None else [_f64(gradp[a]) for a in range(3)]
+    out = np.empty(8)
+    c = make_config(p)
+    st = lib().orc_step_tangent(ctypes.byref(c), s["x"].size, _d(s["x"]), _d(s["y"]),
+                                _d(s["z"]), _d(s["u"]), _d(s["v"]), _d(s["w"]), _d(d), _d(om),
+                                _d(U[0]), _d(U[1]), _d(U[2]), _d(gps[0]), _d(gps[1]),
+                                _d(gps[2]), int(nsteps), _d(out))
+    return out[:2].copy(), np.stack([out[2:5], out[5:8]]), int(st)
