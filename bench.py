@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of the MP-PIC parcel-grid coupling step on GB300.
+
+A "step" is one pass of the whole hot path over the bed: deposit of the solids volume,
+node fields, interpolation, Wen-Yu drag, stress gradient, drag-sum deposit, push with wall
+reflection, re-binning, objectives, and the sort by cell every --sort-every steps. The
+default workload is the dense bed: 128x128x512 cells of 1 cm, 32M parcels filling the
+bottom quarter at solids fraction 0.5 (lognormal d, median 100 um, sigma 0.4), inflow
+0.8 m/s, FP32 state with exact fixed-point deposits, sorted every 10 steps.
+
+Prints one JSON line. `value` is whole-job parcel-updates/s with inputs resident in HBM
+(CUDA events on the library's stream around exactly --steps steps). `e2e` is the same
+metric through the C ABI with the parcel state copied from pinned host memory before and
+back after every step. `roofline` is the fused step kernel's algorithmic bytes per launch
+over its event-timed duration against the measured HBM copy bandwidth. `cpu_baseline` is
+the FP64 CPU oracle on a bounded sample of the same bed.
+
+--impl reference times the oracle itself (the slow program this build is checked
+against) on a bounded sample per step, with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "parcel-updates/s and % HBM roofline, FP32 vs FP64 form on one GB300, at stated err"
+UNIT = "parcel-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--workload", choices=("dense", "fourier", "settle", "grad"), default="dense")
+    ap.add_argument("--np", type=int, default=None, help="override the parcel count")
+    ap.add_argument("--sort-every", type=int, default=10)
+    ap.add_argument("--precision", type=int, choices=(32, 64), default=32)
+    ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64-form comparison (0 = skip)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="parcels in the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, np_override=None, seed_offset=0):
+    from paper_2211_15605_gb300 import synth
+    kw = {}
+    if np_override:
+        kw["n"] = np_override
+    if name == "dense":
+        bed = synth.dense_bed(seed=synth.SEED_BASE + 3 + 1000 * seed_offset, **kw)
+    elif name == "fourier":
+        bed = synth.fourier_bed(seed=synth.SEED_BASE + 2 + 1000 * seed_offset, **kw)
+    elif name == "settle":
+        bed = synth.settle_bed(seed=synth.SEED_BASE + 1 + 1000 * seed_offset, **kw)
+    else:
+        bed = synth.grad_bed(seed=synth.SEED_BASE + 5 + 1000 * seed_offset, **kw)
+    return bed
+
+
+def workload_config(bed, args):
+    p = bed.params
+    return {"workload": bed.meta["workload"], "parcels": bed.np,
+            "grid": [p["nx"], p["ny"], p["nz"]], "cell_m": p["dx"], "sort_every": args.sort_every,
+            "state": "fp32" if args.precision == 32 else "fp64",
+            "deposit": "exact fixed point (int64)" if args.precision == 32 else "exact fixed point (int128)",
+            "l2": "inputs larger than L2 (parcel state %.2f GB)" % (bed.np * (36 if args.precision == 32 else 68) / 1e9)}
+
+
+# ------------------------------------------------------------------ clocks --
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- GPU arm --
+
+def bytes_per_launch(np_, active_bricks, precision):
+    """Algorithmic DRAM bytes of one fused step launch: every parcel's state read once
+    (x,y,z,u,v,w,d,w: 8 values) and written once (x,y,z,u,v,w: 6 values), plus per occupied
+    brick its node-field tile read once (5 fields x 405 nodes) and its five accumulator
+    planes written once (405 nodes)."""
+    t = 4 if precision == 32 else 8
+    words = 1 if precision == 32 else 2
+    per_parcel = 14 * t
+    per_brick = 405 * (5 * t + 5 * 8 * words)
+    return np_ * per_parcel + active_bricks * per_brick
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2211_15605_gb300 import mppic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    bed = make_workload(args.workload, args.np, seed_offset=rank)
+    stream = torch.cuda.current_stream()
+    b = mppic.Bed(bed.params, precision=args.precision, sort_every=args.sort_every, stream=stream)
+    parcels = mppic.parcels_to_device(bed.parcels, args.precision, device=dev)
+    gas = mppic.gas_to_device(bed.U, None, args.precision, device=dev)
+    nsteps_all = args.warmup + args.steps
+    obj = torch.zeros((max(nsteps_all, 1), 2), dtype=torch.float64, device=dev)
+
+    # warm-up steps, then exactly --steps timed steps in one call
+    if args.warmup:
+        b.step(parcels, gas, args.warmup, obj[: args.warmup])
+    b.check()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    b.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(parcels, gas, args.steps, obj[args.warmup:])
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = b.profile_read()
+    b.profile(False)
+    b.check()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * bed.np * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (the fused step kernel)
+    peak, peak_kind = measured_peak()
+    n_step = max(prof["launches"]["step"], 1)
+    step_ms = prof["ms"]["step"] / n_step
+    bpl = bytes_per_launch(bed.np, prof["active_bricks"], args.precision)
+    achieved = bpl / (step_ms / 1e3) / 1e9
+    shares = {k: round(v / max(sum(prof["ms"].values()), 1e-9), 4) for k, v in prof["ms"].items()}
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_brick<float,1> (fused interp/drag/push/deposit)" if args.precision == 32
+                else "k_brick<double,1>", "peak_kind": peak_kind + " (hbm_gbs copy burst)",
+                "bytes_per_launch": bpl, "ms_per_launch": round(step_ms, 5), "phase_ms": prof["ms"],
+                "phase_share": shares}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        fields = mppic.PARCEL_FIELDS
+        host = {k: parcels[k].cpu().pin_memory() for k in fields}
+        out_host = {k: torch.empty_like(host[k]).pin_memory() for k in ("x", "y", "z", "u", "v", "w")}
+        obj_host = torch.empty((1, 2), dtype=torch.float64).pin_memory()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.e2e_steps):
+            for k in fields:
+                parcels[k].copy_(host[k], non_blocking=True)
+            o = b.step(parcels, gas, 1, obj[:1])
+            for k in out_host:
+                out_host[k].copy_(parcels[k], non_blocking=True)
+            obj_host.copy_(o, non_blocking=True)
+        f1.record(stream)
+        barrier()
+        ems = f0.elapsed_time(f1)
+        t2 = torch.tensor([ems], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+        tsz = 4 if args.precision == 32 else 8
+        e2e = {"value": world * bed.np * args.e2e_steps / (float(t2.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": bed.np * 8 * tsz, "d2h_bytes_per_step": bed.np * 6 * tsz + 16,
+               "steps": args.e2e_steps}
+        b.check()
+
+    # FP64 form on the same bed, for the FP32-vs-FP64 comparison
+    fp64 = None
+    if args.fp64_steps > 0 and args.precision == 32 and world == 1:
+        del parcels
+        torch.cuda.empty_cache()
+        b64 = mppic.Bed(bed.params, precision=64, sort_every=args.sort_every, stream=stream)
+        p64 = mppic.parcels_to_device(bed.parcels, 64, device=dev)
+        g64 = mppic.gas_to_device(bed.U, None, 64, device=dev)
+        b64.step(p64, g64, 1)
+        b64.check()
+        barrier()
+        b64.profile(True)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        b64.step(p64, g64, args.fp64_steps)
+        g1.record(stream)
+        barrier()
+        pr64 = b64.profile_read()
+        b64.check()
+        fms = g0.elapsed_time(g1)
+        fp64 = {"value": bed.np * args.fp64_steps / (fms / 1e3), "unit": UNIT,
+                "ms_per_step": fms / args.fp64_steps, "steps": args.fp64_steps,
+                "step_kernel_ms": pr64["ms"]["step"] / max(pr64["launches"]["step"], 1),
+                "bound": "fp64 alu (GB300 FP64 rate)"}
+        b64.close()
+        del p64
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(bed, args.cpu_sample, steps=2)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+                "config": workload_config(bed, args), "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": prof["total_launches"], "clocks": clk,
+                "fp64_form": fp64, "parallelism": "replicas" if world > 1 else "single"}
+        print(json.dumps(line))
+    b.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------- CPU side --
+
+def _sample(bed, m):
+    import numpy as np
+    m = min(m, bed.np)
+    return {k: np.ascontiguousarray(v[:m]) for k, v in bed.parcels.items()}, m
+
+
+def cpu_baseline(bed, m, steps=2):
+    """The FP64 oracle, as it stands (single thread), on the first m parcels of the bed over
+    the full grid for a few steps: parcel-updates/s of the sample."""
+    import oracle
+    oracle.build()
+    sample, m = _sample(bed, m)
+    t0 = time.perf_counter()
+    _, _, st = oracle.step(bed.params, sample, steps, U=bed.U, outputs=False)
+    dt = time.perf_counter() - t0
+    return {"value": m * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{m} of {bed.np} parcels, {steps} steps, full "
+                      f"{bed.params['nx']}x{bed.params['ny']}x{bed.params['nz']} grid, status {st}",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """Time the FP64 CPU oracle on a bounded sample per step (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    bed = make_workload(args.workload, args.np)
+    sample, m = _sample(bed, max(1, args.cpu_sample // 4))
+    state = sample
+    for _ in range(args.warmup):
+        state, _, _ = oracle.step(bed.params, state, 1, U=bed.U, outputs=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        state, _, _ = oracle.step(bed.params, state, 1, U=bed.U, outputs=False)
+    dt = time.perf_counter() - t0
+    value = m * args.steps / dt
+    cfg = workload_config(bed, args)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{m} of {bed.np} parcels per step, full grid"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

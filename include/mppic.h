@@ -1,0 +1,168 @@
+/*
+ * mppic.h - C ABI of libmppic, the GB300 (sm_103a) MP-PIC parcel-grid coupling step.
+ *
+ * The library advances the parcel side of the multiphase particle-in-cell model of
+ * Woo et al., "Development of an Equation-based Parallelization Method for Multiphase
+ * Particle-in-Cell Simulations" (arXiv 2211.15605), Sec. 2.1:
+ *   Eq. 3   dx_P/dt = u_P
+ *   Eq. 4   eps_P rho_P du_P/dt = -eps_P grad p + F_P + eps_P rho_P g - grad tau_P
+ *   Eq. 5   tau_P = p_s eps_P^beta / max[eps_CP - eps_P, alpha (1 - eps_P)]
+ * with the parcel volume V = w * V_particle (Sec. 2.1) and the drag force F of Eq. 2
+ * deposited back to the mesh (Sec. 2.1, explicit coupling of Sec. 2.2.2).
+ * The gas is prescribed (no SIMPLE solve). Drag is Wen-Yu; interpolation is trilinear
+ * cloud-in-cell on the node grid; walls reflect specularly at the parcel centre.
+ *
+ * Geometry: box [0, nx*dx] x [0, ny*dy] x [0, nz*dz]. Cells (i,j,k), 0 <= i < nx, with
+ * row-major id i + nx*(j + ny*k). Nodes (i,j,k), 0 <= i <= nx, with index
+ * i + (nx+1)*(j + (ny+1)*k). Node control volume = dx*dy*dz halved once per axis on
+ * which the node lies on a boundary plane.
+ *
+ * Conventions for every call:
+ *   - Array pointers are DEVICE pointers owned by the caller unless stated otherwise.
+ *     Parcel and node arrays hold float (precision 32) or double (precision 64).
+ *   - Calls are asynchronous on the stream given to mppic_create. A call returns after
+ *     enqueuing its work; host-side argument errors are returned at once.
+ *   - Errors detected on the device (a parcel still outside the box after reflection,
+ *     a non-finite value, a fixed-point accumulator out of range) never trap: they set
+ *     a flag that mppic_check() returns at the next synchronisation.
+ *   - No exception crosses the ABI. mppic_last_error() describes the last failure.
+ *   - The handle owns all scratch (sort buffers, fixed-point accumulators, node fields,
+ *     objective partials); it is freed by mppic_destroy.
+ */
+#ifndef MPPIC_H
+#define MPPIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mppic_handle mppic_handle;
+
+typedef enum {
+  MPPIC_OK = 0,
+  MPPIC_ERR_INVALID = 1,  /* bad argument or configuration (host check) */
+  MPPIC_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+  MPPIC_ERR_OOM = 3,      /* device allocation failed */
+  MPPIC_ERR_DOMAIN = 4,   /* a parcel left the box after reflection, or a value became non-finite */
+  MPPIC_ERR_TIMEOUT = 5,  /* a bounded device loop gave up */
+  MPPIC_ERR_RANGE = 6     /* a fixed-point node accumulator exceeded its range */
+} mppic_status;
+
+/* Parameters of one bed. Paper symbols in brackets. */
+typedef struct {
+  int nx, ny, nz;        /* cells per axis */
+  int precision;         /* 32: FP32 parcel state, interp, drag and push (deposits stay exact
+                            fixed point); 64: FP64 throughout */
+  double dx, dy, dz;     /* cell size [m] */
+  double rho_g, mu_g;    /* gas density [rho_G], viscosity */
+  double g[3];           /* gravity [g] */
+  double gradp[3];       /* uniform pressure gradient [grad p], used when mppic_gas has none */
+  double rho_p;          /* parcel material density [rho_P] */
+  double Ps, beta, eps_cp, alpha; /* Eq. 5 [p_s, beta, eps_CP, alpha] */
+  double eps_g_min;      /* voidage floor for u_g = U / eps_g and for the drag */
+  double e_wall;         /* wall restitution of the specular reflection */
+  double drag_mult;      /* C: multiplies the Wen-Yu drag coefficient */
+  double dscale;         /* s_d: multiplies every parcel diameter */
+  double u_in;           /* added to the z superficial gas velocity at every node */
+  double dt;             /* time step [s] */
+  int sort_every;        /* mppic_step sorts parcels by cell every this many steps;
+                            0 = only when the handle has no valid order */
+  int reserved;
+} mppic_config;
+
+/* Parcel state, structure of arrays, np entries each (caller-owned device memory).
+ * x,y,z,u,v,w,d,omega are float or double per the precision. cell receives the row-major
+ * cell id of each parcel's current position. Sorting permutes every array together;
+ * pid (optional, may be NULL) lets the caller follow parcel identity through sorts. */
+typedef struct {
+  void *x, *y, *z, *u, *v, *w, *d, *omega;
+  int32_t *cell;
+  int32_t *pid;
+  long long np;
+} mppic_parcels;
+
+/* Prescribed gas at the nodes (caller-owned device arrays of (nx+1)(ny+1)(nz+1) values in
+ * the parcel precision). U is the superficial velocity before u_in is added; a NULL
+ * component is zero. gradp all NULL means the uniform gradient of the config. */
+typedef struct {
+  const void *U[3];
+  const void *gradp[3];
+} mppic_gas;
+
+/* Create a handle for one bed (nbeds must be 1; bed_parcel_offsets and per_bed must be
+ * NULL). stream is a cudaStream_t (NULL = legacy default stream). The handle binds to
+ * the current CUDA device. Returns MPPIC_ERR_INVALID for sizes whose cell or node count
+ * overflows int32, non-positive spacing or dt, or an unknown precision. */
+mppic_status mppic_create(const mppic_config *cfg, int nbeds, const long long *bed_parcel_offsets,
+                          const mppic_config *per_bed, void *stream, mppic_handle **out);
+
+/* Step a1-a3 (binning; optional sort by cell). Writes parcels->cell from the positions
+ * with the exact FP64 formula i = clamp(floor(fl64(x * fl64(1/dx))), 0, nx-1).
+ * If do_sort != 0, stably sorts all parcel arrays by a brick-major cell key (bricks of
+ * 8x8x4 cells; within a brick, by cell) and records the cell ranges in the handle. */
+mppic_status mppic_bin(mppic_handle *h, mppic_parcels *parcels, int do_sort);
+
+/* Steps a4-a5: deposit the solids volume of every parcel (V = w pi (s_d d)^3 / 6, trilinear
+ * weights) and form the node fields eps_s, u_g = U / max(1 - eps_s, eps_g_min) and tau
+ * (Eq. 5), kept in the handle. Vs_out (device, double[nnode], may be NULL) receives the
+ * deposited volume. fields_out (device, may be NULL) receives 5 arrays of nnode values in the
+ * parcel precision, back to back: eps_s, u_g,x, u_g,y, u_g,z, tau. gas may be NULL (U = 0). */
+mppic_status mppic_deposit(mppic_handle *h, const mppic_parcels *parcels, const mppic_gas *gas,
+                           double *Vs_out, void *fields_out);
+
+/* Steps a4-a6: deposit, node fields, then interpolation to every parcel. out (device,
+ * 10*np values in the parcel precision, back to back): eps_s, u_g[3], grad p[3],
+ * grad tau[3] (the exact gradient of the trilinear interpolant of the node stresses). */
+mppic_status mppic_interp(mppic_handle *h, const mppic_parcels *parcels, const mppic_gas *gas,
+                          void *out);
+
+/* Steps a1-a10 for nsteps explicit coupling steps, in place. Each step deposits the solids
+ * volume, forms the node fields, and per parcel interpolates, evaluates Wen-Yu drag and the
+ * stress gradient, deposits the drag sums A = sum f W and B = sum f u W (f = rho_p V D),
+ * pushes semi-implicitly (Eq. 4, drag implicit) with Eq. 3, reflects at the walls and
+ * re-bins. obj_out (device, double[2*nsteps], may be NULL) receives per step the pressure
+ * drop dP = sum_p f s_z / (Lx Ly) and the bed height H = 2 sum V z / sum V of the pre-push
+ * state. Parcels are re-sorted every cfg.sort_every steps. */
+mppic_status mppic_step(mppic_handle *h, mppic_parcels *parcels, const mppic_gas *gas,
+                        int nsteps, double *obj_out);
+
+/* The drag sums of the last step of the last mppic_step call, as doubles (device arrays of
+ * nnode values; any may be NULL): A and B[3]. */
+mppic_status mppic_drag_sums(mppic_handle *h, double *A, double *Bx, double *By, double *Bz);
+
+/* Synchronise the handle's stream and return (and clear) any device-side error flag:
+ * MPPIC_OK, MPPIC_ERR_DOMAIN or MPPIC_ERR_RANGE. */
+mppic_status mppic_check(mppic_handle *h);
+
+/* Per-phase timing of the handle's kernels, taken with CUDA events recorded on the
+ * handle's stream around each launch while profiling is enabled. */
+typedef struct {
+  double ms[6];              /* accumulated milliseconds: sort, deposit, finalize, step (the
+                                fused interp/drag/push/deposit kernel), reduce, other */
+  long long launches[6];     /* kernel launches per phase */
+  long long total_launches;  /* all kernels the handle launched while profiling */
+  long long active_bricks;   /* bricks (8x8x4 cells) holding parcels at the last sort */
+  long long parcels;         /* parcel count at the last sort */
+} mppic_profile;
+
+/* Enable (1) or disable (0) per-phase event timing and reset the counters. */
+mppic_status mppic_profile_enable(mppic_handle *h, int enable);
+
+/* Synchronise the stream and return the counters accumulated since enabling. */
+mppic_status mppic_profile_read(mppic_handle *h, mppic_profile *out);
+
+/* Node count (nx+1)(ny+1)(nz+1) of the handle's bed. */
+long long mppic_num_nodes(const mppic_handle *h);
+
+void mppic_destroy(mppic_handle *h);
+
+/* Human-readable description of the handle's last error; h may be NULL (creation errors). */
+const char *mppic_last_error(const mppic_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPPIC_H */

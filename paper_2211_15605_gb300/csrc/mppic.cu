@@ -1,0 +1,605 @@
+// libmppic host side: the C ABI declared in include/mppic.h.
+//
+// The handle owns the scratch of the coupling step (sort buffers, the sorted copy of
+// the parcel arrays, cell ranges, fixed-point node accumulators, node fields and the
+// objective partials) and enqueues every kernel on one stream. Nothing here computes
+// step arithmetic on the host: host code only validates arguments, sizes scratch and
+// launches the kernels of mppic_device.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mppic.h"
+#include "mppic_device.cuh"
+
+using namespace mppic;
+
+struct mppic_handle {
+  mppic_config cfg;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0;
+  long long nnode = 0, nbricks = 0, nkeys = 0;
+  int key_bits = 0;
+  size_t tsize = 4;          // sizeof parcel scalar
+  int words = 1;             // fixed-point words per accumulator
+  // grid-sized scratch
+  u64* acc = nullptr;        // [NQ][words][nnode]
+  void* fld = nullptr;       // 5 x nnode T
+  int* cstart = nullptr;     // nkeys + 1
+  double* obj_part = nullptr;  // 3 x nbricks
+  double* obj_tmp = nullptr;   // 2 doubles (objectives when the caller passes none)
+  int* errs = nullptr;
+  // parcel-sized scratch
+  long long cap = 0;
+  uint32_t* keys[2] = {nullptr, nullptr};
+  uint32_t* vals[2] = {nullptr, nullptr};
+  uint32_t* hist = nullptr;
+  uint32_t* totals = nullptr;
+  void* sorted[8] = {};
+  int* sorted_pid = nullptr;
+  bool sorted_pid_ok = false;
+  // ordering state
+  long long order_np = -1;   // parcel count the cell ranges were built for
+  bool order_on_caller = false;
+  long long step_counter = 0;
+  // last gas seen by deposit (node grad p arrays are read by later pushes)
+  mppic_gas gas{};
+  // profiling: event pairs recorded around each phase while enabled
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;         // start/stop pairs
+  std::vector<int> ev_phase;
+  size_t ev_used = 0;
+  long long launches[6] = {0, 0, 0, 0, 0, 0};
+  long long total_launches = 0;
+  char err[512] = {0};
+};
+
+enum { PH_SORT = 0, PH_DEPOSIT = 1, PH_FINALIZE = 2, PH_STEP = 3, PH_REDUCE = 4, PH_OTHER = 5 };
+
+static char g_create_err[512] = {0};
+
+namespace {
+
+mppic_status fail(mppic_handle* h, mppic_status s, const char* fmt, ...) {
+  char* buf = h ? h->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? MPPIC_ERR_OOM : MPPIC_ERR_CUDA,    \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
+  } while (0)
+
+#define LAUNCHED()                                                                        \
+  do {                                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                  \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, MPPIC_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Records a CUDA event pair around one phase on the handle's stream while profiling is
+// enabled, and counts the phase's kernel launches.
+struct Phase {
+  mppic_handle* h;
+  int phase;
+  size_t slot = (size_t)-1;
+  Phase(mppic_handle* h_, int ph) : h(h_), phase(ph) {
+    if (!h->prof) return;
+    if (h->ev_used * 2 + 2 > h->ev.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+      h->ev.push_back(a);
+      h->ev.push_back(b);
+      h->ev_phase.push_back(ph);
+    }
+    slot = h->ev_used++;
+    h->ev_phase[slot] = ph;
+    cudaEventRecord(h->ev[2 * slot], h->stream);
+  }
+  void launched(int n = 1) {
+    if (!h->prof) return;
+    h->launches[phase] += n;
+    h->total_launches += n;
+  }
+  ~Phase() {
+    if (slot != (size_t)-1) cudaEventRecord(h->ev[2 * slot + 1], h->stream);
+  }
+};
+
+template <class T>
+KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
+  const mppic_config& c = h->cfg;
+  KParams<T> p;
+  memset(&p, 0, sizeof(p));
+  p.nx = c.nx; p.ny = c.ny; p.nz = c.nz;
+  p.nbx = h->nbx; p.nby = h->nby; p.nbz = h->nbz;
+  p.nnode = h->nnode;
+  p.nbricks = h->nbricks;
+  const double hs[3] = {c.dx, c.dy, c.dz};
+  const int ns[3] = {c.nx, c.ny, c.nz};
+  for (int a = 0; a < 3; ++a) {
+    p.inv_d[a] = 1.0 / hs[a];
+    p.inv_f[a] = (float)p.inv_d[a];
+    p.inv_lo[a] = (float)(p.inv_d[a] - (double)p.inv_f[a]);
+    p.invh[a] = (T)p.inv_d[a];
+    p.L[a] = (T)(ns[a] * hs[a]);
+    p.g[a] = (T)c.g[a];
+    p.gp[a] = (T)c.gradp[a];
+  }
+  p.vcell = c.dx * c.dy * c.dz;
+  p.rho_g = (T)c.rho_g; p.mu_g = (T)c.mu_g; p.rho_p = (T)c.rho_p;
+  p.Ps = (T)c.Ps; p.beta = (T)c.beta; p.eps_cp = (T)c.eps_cp; p.alpha = (T)c.alpha;
+  p.eg_min = (T)c.eps_g_min; p.e_wall = (T)c.e_wall; p.C = (T)c.drag_mult; p.sd = (T)c.dscale;
+  p.dt = (T)c.dt; p.u_in = (T)c.u_in;
+  p.vcoef = (T)(M_PI / 6.0 * c.dscale * c.dscale * c.dscale);
+  // Fixed-point units: Vs in cell volumes, A and B in rho_p * cell volume per second.
+  const int SV = sizeof(T) == 4 ? 48 : 96, SA = sizeof(T) == 4 ? 40 : 88;
+  double mV = std::ldexp(1.0, SV) / p.vcell;
+  double mA = std::ldexp(1.0, SA) / (c.rho_p * p.vcell);
+  p.mV = (T)mV; p.mA = (T)mA;
+  p.inv_mV = 1.0 / (double)p.mV; p.inv_mA = 1.0 / (double)p.mA;
+  T* f = static_cast<T*>(h->fld);
+  for (int k = 0; k < 5; ++k) p.fld[k] = f + (long long)k * h->nnode;
+  p.has_gp = 0;
+  if (gas) {
+    for (int a = 0; a < 3; ++a) p.U[a] = static_cast<const T*>(gas->U[a]);
+    if (gas->gradp[0] && gas->gradp[1] && gas->gradp[2]) {
+      p.has_gp = 1;
+      for (int a = 0; a < 3; ++a) p.gpf[a] = static_cast<const T*>(gas->gradp[a]);
+    }
+  }
+  p.acc = h->acc;
+  p.errs = h->errs;
+  p.cstart = h->cstart;
+  return p;
+}
+
+template <class T>
+PArrays<T> caller_arrays(const mppic_parcels* pc) {
+  PArrays<T> a;
+  void* const src[8] = {pc->x, pc->y, pc->z, pc->u, pc->v, pc->w, pc->d, pc->omega};
+  for (int f = 0; f < 8; ++f) a.a[f] = static_cast<T*>(src[f]);
+  a.pid = pc->pid;
+  return a;
+}
+
+template <class T>
+PArrays<T> sorted_arrays(mppic_handle* h, bool with_pid) {
+  PArrays<T> a;
+  for (int f = 0; f < 8; ++f) a.a[f] = static_cast<T*>(h->sorted[f]);
+  a.pid = with_pid ? h->sorted_pid : nullptr;
+  return a;
+}
+
+mppic_status check_parcels(mppic_handle* h, const mppic_parcels* pc) {
+  if (!pc) return fail(h, MPPIC_ERR_INVALID, "parcels is NULL");
+  if (pc->np < 0 || pc->np > 0x7fffffffLL)
+    return fail(h, MPPIC_ERR_INVALID, "np=%lld out of range [0, 2^31)", pc->np);
+  if (pc->np > 0 && (!pc->x || !pc->y || !pc->z || !pc->u || !pc->v || !pc->w || !pc->d ||
+                     !pc->omega))
+    return fail(h, MPPIC_ERR_INVALID, "a parcel array is NULL");
+  return MPPIC_OK;
+}
+
+mppic_status ensure_capacity(mppic_handle* h, long long np, bool want_pid) {
+  if (np <= h->cap && (!want_pid || h->sorted_pid)) return MPPIC_OK;
+  long long cap = np > h->cap ? np : h->cap;
+  if (cap > h->cap) {
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(h->keys[i]); cudaFree(h->vals[i]);
+      h->keys[i] = h->vals[i] = nullptr;
+    }
+    cudaFree(h->hist); h->hist = nullptr;
+    for (int f = 0; f < 8; ++f) { cudaFree(h->sorted[f]); h->sorted[f] = nullptr; }
+    cudaFree(h->sorted_pid); h->sorted_pid = nullptr;
+    h->cap = 0;
+    long long nblk = (cap + SORT_TILE - 1) / SORT_TILE;
+    for (int i = 0; i < 2; ++i) {
+      CU(cudaMalloc(&h->keys[i], sizeof(uint32_t) * cap));
+      CU(cudaMalloc(&h->vals[i], sizeof(uint32_t) * cap));
+    }
+    CU(cudaMalloc(&h->hist, sizeof(uint32_t) * 256 * (nblk > 0 ? nblk : 1)));
+    for (int f = 0; f < 8; ++f) CU(cudaMalloc(&h->sorted[f], h->tsize * cap));
+    h->cap = cap;
+  }
+  if (want_pid && !h->sorted_pid) CU(cudaMalloc(&h->sorted_pid, sizeof(int) * h->cap));
+  return MPPIC_OK;
+}
+
+// Sort the parcels currently in `cur` by brick-major cell key into the handle's sorted
+// copy, and rebuild the cell ranges. Leaves the sorted copy as the parcel source.
+template <class T>
+mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays<T> cur) {
+  const long long np = pc->np;
+  mppic_status s = ensure_capacity(h, np, pc->pid != nullptr);
+  if (s) return s;
+  KParams<T> p = make_params<T>(h, nullptr);
+  cudaStream_t st = h->stream;
+  Phase ph(h, PH_SORT);
+  if (np > 0) {
+    k_keys<T><<<blocks(np, 256), 256, 0, st>>>(p, cur.a[0], cur.a[1], cur.a[2], h->keys[0],
+                                                h->vals[0], np);
+    LAUNCHED();
+    const int nblk = (int)((np + SORT_TILE - 1) / SORT_TILE);
+    const int passes = (h->key_bits + 7) / 8;
+    int src = 0;
+    for (int ps = 0; ps < passes; ++ps) {
+      const int shift = 8 * ps;
+      k_sort_hist<<<nblk, SORT_THREADS, 0, st>>>(h->keys[src], np, shift, h->hist, nblk);
+      k_sort_scan<<<256, 1024, 0, st>>>(h->hist, nblk, h->totals);
+      k_sort_scatter<<<nblk, SORT_THREADS, 0, st>>>(h->keys[src], h->vals[src], h->keys[1 - src],
+                                                     h->vals[1 - src], np, shift, h->hist,
+                                                     h->totals, nblk);
+      LAUNCHED();
+      ph.launched(3);
+      src = 1 - src;
+    }
+    k_gather<T><<<blocks(np, 256), 256, 0, st>>>(cur, sorted_arrays<T>(h, cur.pid != nullptr),
+                                                  h->vals[src], np);
+    LAUNCHED();
+    k_cell_starts<<<blocks(h->nkeys + 1, 256), 256, 0, st>>>(h->keys[src], np, h->nkeys,
+                                                             h->cstart);
+    ph.launched(3);
+  } else {
+    CU(cudaMemsetAsync(h->cstart, 0, sizeof(int) * (h->nkeys + 1), st));
+  }
+  LAUNCHED();
+  h->order_np = np;
+  h->sorted_pid_ok = pc->pid != nullptr;
+  return MPPIC_OK;
+}
+
+template <class T>
+mppic_status launch_brick(mppic_handle* h, int mode, const KParams<T>& p, PArrays<T> src,
+                          PArrays<T> dst, int* cell_out) {
+  const size_t sm = BrickSmem<T>::bytes;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[mode]) {
+    if (mode == 0)
+      CU(cudaFuncSetAttribute(k_brick<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    else
+      CU(cudaFuncSetAttribute(k_brick<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_set[mode] = true;
+  }
+  if (h->nbricks == 0) return MPPIC_OK;
+  Phase ph(h, mode == 0 ? PH_DEPOSIT : PH_STEP);
+  ph.launched();
+  if (mode == 0)
+    k_brick<T, 0><<<(unsigned)h->nbricks, BCELLS, sm, h->stream>>>(p, src, dst, nullptr,
+                                                                   h->obj_part);
+  else
+    k_brick<T, 1><<<(unsigned)h->nbricks, BCELLS, sm, h->stream>>>(p, src, dst, cell_out,
+                                                                   h->obj_part);
+  LAUNCHED();
+  return MPPIC_OK;
+}
+
+// Deposit the solids volume of the given parcels (order from the handle, sorting into the
+// scratch copy if the caller's arrays carry no valid order) and form the node fields.
+template <class T>
+mppic_status deposit_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_gas* gas,
+                          double* vs_out) {
+  PArrays<T> cur = caller_arrays<T>(pc);
+  PArrays<T> src = cur;
+  if (!h->order_on_caller || h->order_np != pc->np) {
+    mppic_status s = sort_into_scratch<T>(h, pc, cur);
+    if (s) return s;
+    src = sorted_arrays<T>(h, pc->pid != nullptr);
+    h->order_on_caller = false;
+  }
+  KParams<T> p = make_params<T>(h, gas);
+  mppic_status s = launch_brick<T>(h, 0, p, src, src, nullptr);
+  if (s) return s;
+  {
+    Phase ph(h, PH_FINALIZE);
+    ph.launched();
+    k_finalize<T><<<blocks(h->nnode, 256), 256, 0, h->stream>>>(p, vs_out);
+    LAUNCHED();
+  }
+  if (gas) h->gas = *gas; else memset(&h->gas, 0, sizeof(h->gas));
+  return MPPIC_OK;
+}
+
+template <class T>
+mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas, int nsteps,
+                       double* obj_out) {
+  const long long np = pc->np;
+  PArrays<T> dst = caller_arrays<T>(pc);
+  PArrays<T> src = dst;
+  const int every = h->cfg.sort_every;
+  auto sort_due = [&](long long step) { return every > 0 && step % every == 0; };
+  if (!h->order_on_caller || h->order_np != np || sort_due(h->step_counter)) {
+    mppic_status s = sort_into_scratch<T>(h, pc, dst);
+    if (s) return s;
+    src = sorted_arrays<T>(h, pc->pid != nullptr);
+  }
+  KParams<T> p = make_params<T>(h, gas);
+  mppic_status s = launch_brick<T>(h, 0, p, src, src, nullptr);   // Vs of the current positions
+  if (s) return s;
+  const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
+  for (int it = 0; it < nsteps; ++it) {
+    if (it > 0 && sort_due(h->step_counter + it)) {
+      s = sort_into_scratch<T>(h, pc, dst);
+      if (s) return s;
+      src = sorted_arrays<T>(h, pc->pid != nullptr);
+    }
+    {
+      Phase ph(h, PH_FINALIZE);
+      ph.launched();
+      k_finalize<T><<<blocks(h->nnode, 256), 256, 0, h->stream>>>(p, nullptr);
+      LAUNCHED();
+    }
+    s = launch_brick<T>(h, 1, p, src, dst, it == nsteps - 1 ? pc->cell : nullptr);
+    if (s) return s;
+    src = dst;
+    {
+      Phase ph(h, PH_REDUCE);
+      ph.launched();
+      k_obj_reduce<<<1, 1024, 0, h->stream>>>(h->obj_part, h->nbricks, area,
+                                              obj_out ? obj_out + 2 * it : h->obj_tmp);
+      LAUNCHED();
+    }
+  }
+  if (nsteps == 0 && pc->cell && np > 0) {
+    k_bin<T><<<blocks(np, 256), 256, 0, h->stream>>>(p, dst.a[0], dst.a[1], dst.a[2], pc->cell, np);
+    LAUNCHED();
+  }
+  h->order_on_caller = true;
+  h->order_np = np;
+  h->step_counter += nsteps;
+  if (gas) h->gas = *gas; else memset(&h->gas, 0, sizeof(h->gas));
+  return MPPIC_OK;
+}
+
+template <class T>
+mppic_status bin_impl(mppic_handle* h, mppic_parcels* pc, int do_sort) {
+  const long long np = pc->np;
+  PArrays<T> cur = caller_arrays<T>(pc);
+  if (do_sort) {
+    mppic_status s = sort_into_scratch<T>(h, pc, cur);
+    if (s) return s;
+    if (np > 0) {
+      for (int f = 0; f < 8; ++f)
+        CU(cudaMemcpyAsync(cur.a[f], h->sorted[f], h->tsize * np, cudaMemcpyDeviceToDevice,
+                           h->stream));
+      if (pc->pid)
+        CU(cudaMemcpyAsync(pc->pid, h->sorted_pid, sizeof(int) * np, cudaMemcpyDeviceToDevice,
+                           h->stream));
+    }
+    h->order_on_caller = true;
+  }
+  if (np > 0 && pc->cell) {
+    KParams<T> p = make_params<T>(h, nullptr);
+    k_bin<T><<<blocks(np, 256), 256, 0, h->stream>>>(p, cur.a[0], cur.a[1], cur.a[2], pc->cell, np);
+    LAUNCHED();
+  }
+  return MPPIC_OK;
+}
+
+template <class T>
+mppic_status interp_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_gas* gas, void* out) {
+  mppic_status s = deposit_impl<T>(h, pc, gas, nullptr);
+  if (s) return s;
+  if (pc->np > 0) {
+    KParams<T> p = make_params<T>(h, gas);
+    PArrays<T> cur = caller_arrays<T>(pc);
+    k_interp_out<T><<<blocks(pc->np, 256), 256, 0, h->stream>>>(p, cur.a[0], cur.a[1], cur.a[2],
+                                                                 static_cast<T*>(out), pc->np);
+    LAUNCHED();
+  }
+  return MPPIC_OK;
+}
+
+template <class T>
+mppic_status drag_impl(mppic_handle* h, double* A, double* Bx, double* By, double* Bz) {
+  KParams<T> p = make_params<T>(h, nullptr);
+  k_drag_out<T><<<blocks(h->nnode, 256), 256, 0, h->stream>>>(p, A, Bx, By, Bz);
+  LAUNCHED();
+  return MPPIC_OK;
+}
+
+int bits_for(long long n) {  // bits to represent values 0..n-1
+  int b = 0;
+  while ((1LL << b) < n) ++b;
+  return b < 1 ? 1 : b;
+}
+
+}  // namespace
+
+extern "C" {
+
+mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* bed_parcel_offsets,
+                          const mppic_config* per_bed, void* stream, mppic_handle** out) {
+  mppic_handle* h = nullptr;
+  if (!cfg || !out) return fail(h, MPPIC_ERR_INVALID, "cfg and out must not be NULL");
+  *out = nullptr;
+  if (nbeds != 1 || bed_parcel_offsets || per_bed)
+    return fail(h, MPPIC_ERR_INVALID, "only nbeds == 1 is supported by this entry point");
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1)
+    return fail(h, MPPIC_ERR_INVALID, "grid %dx%dx%d must be at least 1 cell per axis", cfg->nx,
+                cfg->ny, cfg->nz);
+  if (!(cfg->dx > 0 && cfg->dy > 0 && cfg->dz > 0 && cfg->dt > 0))
+    return fail(h, MPPIC_ERR_INVALID, "dx, dy, dz and dt must be positive");
+  if (!(cfg->rho_p > 0 && cfg->rho_g > 0 && cfg->mu_g > 0))
+    return fail(h, MPPIC_ERR_INVALID, "densities and viscosity must be positive");
+  if (cfg->precision != 32 && cfg->precision != 64)
+    return fail(h, MPPIC_ERR_INVALID, "precision must be 32 or 64, got %d", cfg->precision);
+  if (cfg->sort_every < 0) return fail(h, MPPIC_ERR_INVALID, "sort_every must be >= 0");
+  const long long nnode = (long long)(cfg->nx + 1) * (cfg->ny + 1) * (cfg->nz + 1);
+  const long long nbx = (cfg->nx + BX - 1) / BX, nby = (cfg->ny + BY - 1) / BY,
+                  nbz = (cfg->nz + BZ - 1) / BZ;
+  const long long nkeys = nbx * nby * nbz * BCELLS;
+  if (nnode >= 0x7fffffffLL || nkeys >= 0x7fffffffLL)
+    return fail(h, MPPIC_ERR_INVALID, "grid too large: node or key count overflows int32");
+  h = new (std::nothrow) mppic_handle();
+  if (!h) return fail(nullptr, MPPIC_ERR_OOM, "host allocation failed");
+  h->cfg = *cfg;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->nx = cfg->nx; h->ny = cfg->ny; h->nz = cfg->nz;
+  h->nbx = (int)nbx; h->nby = (int)nby; h->nbz = (int)nbz;
+  h->nnode = nnode;
+  h->nbricks = nbx * nby * nbz;
+  h->nkeys = nkeys;
+  h->key_bits = bits_for(nkeys);
+  h->tsize = cfg->precision == 32 ? 4 : 8;
+  h->words = cfg->precision == 32 ? 1 : 2;
+  mppic_status s = MPPIC_OK;
+  auto alloc = [&](void** ptr, size_t bytes) -> bool {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+      s = fail(h, e == cudaErrorMemoryAllocation ? MPPIC_ERR_OOM : MPPIC_ERR_CUDA,
+               "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+      return false;
+    }
+    return true;
+  };
+  if (cudaGetDevice(&h->device) != cudaSuccess) s = fail(h, MPPIC_ERR_CUDA, "no CUDA device");
+  if (!s && alloc((void**)&h->acc, sizeof(u64) * NQ * h->words * nnode) &&
+      alloc(&h->fld, h->tsize * 5 * nnode) && alloc((void**)&h->cstart, sizeof(int) * (nkeys + 1)) &&
+      alloc((void**)&h->obj_part, sizeof(double) * 3 * h->nbricks) &&
+      alloc((void**)&h->obj_tmp, sizeof(double) * 2) && alloc((void**)&h->errs, sizeof(int)) &&
+      alloc((void**)&h->totals, sizeof(uint32_t) * 256)) {
+    cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(u64) * NQ * h->words * nnode, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->errs, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->fld, 0, h->tsize * 5 * nnode, h->stream);
+    if (e != cudaSuccess) s = fail(h, MPPIC_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  }
+  if (s) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
+    mppic_destroy(h);
+    return s;
+  }
+  *out = h;
+  return MPPIC_OK;
+}
+
+mppic_status mppic_bin(mppic_handle* h, mppic_parcels* parcels, int do_sort) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  mppic_status s = check_parcels(h, parcels);
+  if (s) return s;
+  return h->cfg.precision == 32 ? bin_impl<float>(h, parcels, do_sort)
+                                : bin_impl<double>(h, parcels, do_sort);
+}
+
+mppic_status mppic_deposit(mppic_handle* h, const mppic_parcels* parcels, const mppic_gas* gas,
+                           double* Vs_out, void* fields_out) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  mppic_status s = check_parcels(h, parcels);
+  if (s) return s;
+  s = h->cfg.precision == 32 ? deposit_impl<float>(h, parcels, gas, Vs_out)
+                             : deposit_impl<double>(h, parcels, gas, Vs_out);
+  if (s) return s;
+  if (fields_out)
+    CU(cudaMemcpyAsync(fields_out, h->fld, h->tsize * 5 * h->nnode, cudaMemcpyDeviceToDevice,
+                       h->stream));
+  return MPPIC_OK;
+}
+
+mppic_status mppic_interp(mppic_handle* h, const mppic_parcels* parcels, const mppic_gas* gas,
+                          void* out) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  mppic_status s = check_parcels(h, parcels);
+  if (s) return s;
+  if (!out && parcels->np > 0) return fail(h, MPPIC_ERR_INVALID, "out is NULL");
+  return h->cfg.precision == 32 ? interp_impl<float>(h, parcels, gas, out)
+                                : interp_impl<double>(h, parcels, gas, out);
+}
+
+mppic_status mppic_step(mppic_handle* h, mppic_parcels* parcels, const mppic_gas* gas, int nsteps,
+                        double* obj_out) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  mppic_status s = check_parcels(h, parcels);
+  if (s) return s;
+  if (nsteps < 0) return fail(h, MPPIC_ERR_INVALID, "nsteps must be >= 0");
+  return h->cfg.precision == 32 ? step_impl<float>(h, parcels, gas, nsteps, obj_out)
+                                : step_impl<double>(h, parcels, gas, nsteps, obj_out);
+}
+
+mppic_status mppic_drag_sums(mppic_handle* h, double* A, double* Bx, double* By, double* Bz) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  return h->cfg.precision == 32 ? drag_impl<float>(h, A, Bx, By, Bz)
+                                : drag_impl<double>(h, A, Bx, By, Bz);
+}
+
+mppic_status mppic_check(mppic_handle* h) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  CU(cudaStreamSynchronize(h->stream));
+  int flags = 0;
+  CU(cudaMemcpy(&flags, h->errs, sizeof(int), cudaMemcpyDeviceToHost));
+  CU(cudaMemset(h->errs, 0, sizeof(int)));
+  if (flags & ERR_RANGE) return fail(h, MPPIC_ERR_RANGE, "a fixed-point accumulator left its range");
+  if (flags & ERR_DOMAIN)
+    return fail(h, MPPIC_ERR_DOMAIN, "a parcel left the box after reflection or became non-finite");
+  return MPPIC_OK;
+}
+
+mppic_status mppic_profile_enable(mppic_handle* h, int enable) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  CU(cudaStreamSynchronize(h->stream));
+  h->prof = enable != 0;
+  h->ev_used = 0;
+  for (int i = 0; i < 6; ++i) h->launches[i] = 0;
+  h->total_launches = 0;
+  return MPPIC_OK;
+}
+
+mppic_status mppic_profile_read(mppic_handle* h, mppic_profile* out) {
+  if (!h || !out) return fail(h, MPPIC_ERR_INVALID, "handle and out must not be NULL");
+  CU(cudaStreamSynchronize(h->stream));
+  memset(out, 0, sizeof(*out));
+  for (size_t i = 0; i < h->ev_used; ++i) {
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]));
+    out->ms[h->ev_phase[i]] += ms;
+  }
+  for (int i = 0; i < 6; ++i) out->launches[i] = h->launches[i];
+  out->total_launches = h->total_launches;
+  out->parcels = h->order_np > 0 ? h->order_np : 0;
+  if (h->nbricks > 0) {
+    unsigned long long* cnt = nullptr;
+    CU(cudaMalloc(&cnt, sizeof(unsigned long long)));
+    CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), h->stream));
+    k_count_bricks<<<blocks(h->nbricks, 256), 256, 0, h->stream>>>(h->cstart, h->nbricks, cnt);
+    unsigned long long c = 0;
+    cudaError_t e = cudaMemcpyAsync(&c, cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(cnt);
+    if (e != cudaSuccess) return fail(h, MPPIC_ERR_CUDA, "profile read: %s", cudaGetErrorString(e));
+    out->active_bricks = (long long)c;
+  }
+  return MPPIC_OK;
+}
+
+long long mppic_num_nodes(const mppic_handle* h) { return h ? h->nnode : 0; }
+
+void mppic_destroy(mppic_handle* h) {
+  if (!h) return;
+  cudaFree(h->acc); cudaFree(h->fld); cudaFree(h->cstart); cudaFree(h->obj_part);
+  cudaFree(h->obj_tmp); cudaFree(h->errs); cudaFree(h->totals); cudaFree(h->hist);
+  for (int i = 0; i < 2; ++i) { cudaFree(h->keys[i]); cudaFree(h->vals[i]); }
+  for (int f = 0; f < 8; ++f) cudaFree(h->sorted[f]);
+  cudaFree(h->sorted_pid);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  delete h;
+}
+
+const char* mppic_last_error(const mppic_handle* h) { return h ? h->err : g_create_err; }
+
+}  // extern "C"
