@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--workload", choices=("dense", "fourier", "settle", "grad"), default="dense")
     ap.add_argument("--np", type=int, default=None, help="override the parcel count")
+    ap.add_argument("--grid", type=str, default=None, help="override the grid, e.g. 64,64,256")
     ap.add_argument("--sort-every", type=int, default=10)
     ap.add_argument("--precision", type=int, choices=(32, 64), default=32)
     ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64-form comparison (0 = skip)")
@@ -54,11 +55,13 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name, np_override=None, seed_offset=0):
+def make_workload(name, np_override=None, seed_offset=0, grid=None):
     from paper_2211_15605_gb300 import synth
     kw = {}
     if np_override:
         kw["n"] = np_override
+    if grid:
+        kw["nx"], kw["ny"], kw["nz"] = (int(t) for t in grid.split(","))
     if name == "dense":
         bed = synth.dense_bed(seed=synth.SEED_BASE + 3 + 1000 * seed_offset, **kw)
     elif name == "fourier":
@@ -173,7 +176,7 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    bed = make_workload(args.workload, args.np, seed_offset=rank)
+    bed = make_workload(args.workload, args.np, seed_offset=rank, grid=args.grid)
     stream = torch.cuda.current_stream()
     b = mppic.Bed(bed.params, precision=args.precision, sort_every=args.sort_every, stream=stream)
     parcels = mppic.parcels_to_device(bed.parcels, args.precision, device=dev)
@@ -323,7 +326,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    bed = make_workload(args.workload, args.np)
+    bed = make_workload(args.workload, args.np, grid=args.grid)
     sample, m = _sample(bed, max(1, args.cpu_sample // 4))
     state = sample
     for _ in range(args.warmup):

@@ -266,6 +266,13 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
   return MPPIC_OK;
 }
 
+// The Vs accumulator may still hold the deposit a previous push made for positions the
+// caller has since replaced or advanced; a deposit of the current positions starts from zero.
+mppic_status clear_volume_accumulator(mppic_handle* h) {
+  CU(cudaMemsetAsync(h->acc, 0, sizeof(u64) * h->words * h->nnode, h->stream));
+  return MPPIC_OK;
+}
+
 template <class T>
 mppic_status launch_brick(mppic_handle* h, int mode, const KParams<T>& p, PArrays<T> src,
                           PArrays<T> dst, int* cell_out) {
@@ -305,7 +312,9 @@ mppic_status deposit_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_
     h->order_on_caller = false;
   }
   KParams<T> p = make_params<T>(h, gas);
-  mppic_status s = launch_brick<T>(h, 0, p, src, src, nullptr);
+  mppic_status s = clear_volume_accumulator(h);
+  if (s) return s;
+  s = launch_brick<T>(h, 0, p, src, src, nullptr);
   if (s) return s;
   {
     Phase ph(h, PH_FINALIZE);
@@ -331,7 +340,9 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
     src = sorted_arrays<T>(h, pc->pid != nullptr);
   }
   KParams<T> p = make_params<T>(h, gas);
-  mppic_status s = launch_brick<T>(h, 0, p, src, src, nullptr);   // Vs of the current positions
+  mppic_status s = clear_volume_accumulator(h);
+  if (s) return s;
+  s = launch_brick<T>(h, 0, p, src, src, nullptr);   // Vs of the current positions
   if (s) return s;
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   for (int it = 0; it < nsteps; ++it) {

@@ -31,6 +31,26 @@ def host(t):
     return t.detach().double().cpu().numpy()
 
 
+VEL = ("u", "v", "w")
+
+
+def state_errors(dev, ref):
+    """Normwise error of each state field of the device (re-ordered to the original parcel
+    order by pid: mppic_step sorts the caller's arrays) against the oracle. Velocity
+    components share one scale, the largest velocity magnitude of the reference."""
+    order = dev["pid"].cpu().numpy()
+    vscale = max(float(np.max(np.abs(ref[k]))) for k in VEL)
+    out = {}
+    for k in ("x", "y", "z", "u", "v", "w"):
+        got = np.empty_like(ref[k])
+        got[order] = host(dev[k])
+        if k in VEL:
+            out[k] = float(np.max(np.abs(got - ref[k]))) / max(vscale, 1e-300)
+        else:
+            out[k] = normwise(got, ref[k])
+    return out
+
+
 def rounded(parcels, prec):
     """The parcel state as the device stores it (FP32 form: rounded to float), in float64."""
     dt = np.float32 if prec == 32 else np.float64
@@ -154,7 +174,7 @@ def _step_compare(bed, prec, nsteps=1, sort_every=1, gradp_field=False):
     ref, ex, st = oracle.step(p, parcels, nsteps, U=U, gradp=gp)
     assert st == 0
     b = mppic.Bed(p, precision=prec, sort_every=sort_every)
-    dev = mppic.parcels_to_device(parcels, prec)
+    dev = mppic.parcels_to_device(parcels, prec, with_pid=True)
     gas = mppic.gas_to_device(U, gp, prec)
     obj = host(b.step(dev, gas, nsteps))
     A, B = b.drag_sums()
@@ -167,8 +187,8 @@ def test_single_step_all_fields(prec):
     bed = synth.fourier_bed(n=80_000, nx=16, ny=24, nz=40, nsteps=1)
     synth.random_velocities(bed, 0.3, seed=21)
     ref, ex, dev, obj, A, B = _step_compare(bed, prec)
-    for k in ("x", "y", "z", "u", "v", "w"):
-        assert normwise(host(dev[k]), ref[k]) <= TOL[prec], (k, normwise(host(dev[k]), ref[k]))
+    for k, err in state_errors(dev, ref).items():
+        assert err <= TOL[prec], (k, err)
     assert normwise(A, ex["A"]) <= TOL[prec]
     for a in range(3):
         assert normwise(B[a], ex["B"][a]) <= TOL[prec]
@@ -186,8 +206,8 @@ def test_single_step_with_node_pressure_gradient_and_stress(prec):
     bed.params.update(Ps=20.0)
     synth.random_velocities(bed, 0.2, seed=4)
     ref, ex, dev, obj, A, B = _step_compare(bed, prec, gradp_field=True)
-    for k in ("x", "y", "z", "u", "v", "w"):
-        assert normwise(host(dev[k]), ref[k]) <= TOL[prec], k
+    for k, err in state_errors(dev, ref).items():
+        assert err <= TOL[prec], (k, err)
 
 
 @pytest.mark.parametrize("prec", [32, 64])
@@ -199,8 +219,7 @@ def test_few_steps_sort_schedules(prec):
     bed.params["dt"] = 5e-3          # parcels cross cells between sorts
     for every in (1, 3, 0):
         ref, ex, dev, obj, A, B = _step_compare(bed, prec, nsteps=6, sort_every=every)
-        for k in ("x", "y", "z", "u", "v", "w"):
-            err = normwise(host(dev[k]), ref[k])
+        for k, err in state_errors(dev, ref).items():
             assert err <= 10 * TOL[prec], (every, k, err)
         assert normwise(obj[:, 0], ex["obj"][:, 0]) <= 10 * TOL[prec]
 
@@ -236,12 +255,12 @@ def test_empty_and_single_parcel(prec):
                v=np.zeros(1), w=np.array([-0.2]), d=np.array([2e-4]), omega=np.array([10.0]))
     one = rounded(one, prec)
     ref, ex, st = oracle.step(p, one, 3)
-    dev = mppic.parcels_to_device(one, prec)
+    dev = mppic.parcels_to_device(one, prec, with_pid=True)
     b2 = mppic.Bed(p, precision=prec)
     obj = host(b2.step(dev, None, 3))
     b2.check()
-    for k in ("x", "y", "z", "u", "v", "w"):
-        assert normwise(host(dev[k]), ref[k]) <= TOL[prec], k
+    for k, err in state_errors(dev, ref).items():
+        assert err <= TOL[prec], (k, err)
 
 
 @pytest.mark.parametrize("prec", [32, 64])
@@ -255,11 +274,11 @@ def test_parcels_on_walls_and_nodes(prec):
                    w=np.zeros(n), d=np.full(n, 1e-3), omega=np.full(n, 100.0))
     ref, ex, st = oracle.step(p, parcels, 1)
     b = mppic.Bed(p, precision=prec)
-    dev = mppic.parcels_to_device(parcels, prec)
+    dev = mppic.parcels_to_device(parcels, prec, with_pid=True)
     b.step(dev, None, 1)
     b.check()
-    for k in ("x", "y", "z", "u", "v", "w"):
-        assert normwise(host(dev[k]), ref[k]) <= TOL[prec], k
+    for k, err in state_errors(dev, ref).items():
+        assert err <= TOL[prec], (k, err)
 
 
 @pytest.mark.parametrize("prec", [32, 64])
