@@ -153,6 +153,31 @@ mppic_status mppic_profile_enable(mppic_handle *h, int enable);
 /* Synchronise the stream and return the counters accumulated since enabling. */
 mppic_status mppic_profile_read(mppic_handle *h, mppic_profile *out);
 
+/* Largest node count (nx+1)(ny+1)(nz+1) that mppic_deposit_static accepts. */
+#define MPPIC_STATIC_MAX_NODES 524288
+
+/* Solids-volume deposit that allocates nothing. The paper has no counterpart: this entry
+ * point exists for callers that may not call cudaMalloc, such as a host simulation code
+ * that hands the library a fixed device memory pool, or a solve phase in which a device
+ * allocation (and the synchronisation it implies) is not allowed.
+ *
+ * It computes what mppic_deposit writes to Vs_out (Vs_n = sum_p V_p W_pn, as doubles),
+ * without a handle: its fixed-point scratch is one static device array of
+ * MPPIC_STATIC_MAX_NODES x 16 bytes (8 MiB) that every GPU which loads the library holds
+ * until the process exits. Parcels need not be sorted.
+ *   cfg      grid, spacing, dscale and precision of the bed (host pointer)
+ *   parcels  device arrays x, y, z, d, omega of np entries (other fields are not read)
+ *   Vs_out   device array of (nx+1)(ny+1)(nz+1) doubles, written
+ *   stream   cudaStream_t the work is enqueued on (NULL = legacy default stream)
+ * Returns MPPIC_ERR_INVALID, without enqueuing anything, if the node count exceeds
+ * MPPIC_STATIC_MAX_NODES or the arguments are invalid. The first call on each device
+ * looks up the device address of the static array (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. Every call clears and reuses
+ * the same array, so calls that overlap on the GPU (on different streams, or from several
+ * threads) race and produce wrong sums; serialise them. */
+mppic_status mppic_deposit_static(const mppic_config *cfg, const mppic_parcels *parcels,
+                                  double *Vs_out, void *stream);
+
 /* Node count (nx+1)(ny+1)(nz+1) of the handle's bed. */
 long long mppic_num_nodes(const mppic_handle *h);
 

@@ -614,3 +614,121 @@ void mppic_destroy(mppic_handle* h) {
 const char* mppic_last_error(const mppic_handle* h) { return h ? h->err : g_create_err; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------
+// Allocation-free solids-volume deposit (mppic_deposit_static).
+//
+// Its scratch is a file-scope device array, so the entry point never calls cudaMalloc,
+// cudaFree or an allocating library routine. Host code cannot use the array's name as a
+// device address (it names a host-side shadow), so the device address is looked up once
+// per device with cudaGetSymbolAddress and passed to the kernels.
+
+namespace {
+
+constexpr int kStaticWords = 2;                       // FP64 form needs two words per node
+static __device__ __align__(256) unsigned long long
+    g_static_scratch[MPPIC_STATIC_MAX_NODES * kStaticWords + 32];  // + one slot for flags
+
+constexpr int kMaxDevices = 64;
+static void* g_static_addr[kMaxDevices] = {};
+
+// Each parcel adds its 8 fixed-point corner contributions to the static accumulator.
+template <class T>
+__global__ void k_deposit_static(KParams<T> p, const T* __restrict__ x, const T* __restrict__ y,
+                                 const T* __restrict__ z, const T* __restrict__ d,
+                                 const T* __restrict__ om, long long np, u64* acc) {
+  constexpr int W = Words<T>::n;
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= np) return;
+  Cell3<T> c;
+  bin3(p, x[q], y[q], z[q], c);
+  T dq = d[q];
+  T V = om[q] * (dq * dq * dq) * p.vcoef;
+  T w[3][2];
+  for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - c.xi[a]; w[a][1] = c.xi[a]; }
+  for (int cc = 0; cc < 2; ++cc)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        u64 fx[W];
+        to_fixed(V * ((w[0][a] * w[1][b]) * w[2][cc]), p.mV, fx, p.errs);
+        acc_add(acc + node_id(p, c.i + a, c.j + b, c.k + cc), p.nnode, fx);
+      }
+}
+
+template <class T>
+__global__ void k_static_out(const u64* __restrict__ acc, long long nnode, double inv_m,
+                             double* __restrict__ out) {
+  constexpr int W = Words<T>::n;
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= nnode) return;
+  u64 fx[W];
+  for (int w = 0; w < W; ++w) fx[w] = acc[(long long)w * nnode + n];
+  out[n] = from_fixed(fx, inv_m);
+}
+
+template <class T>
+mppic_status deposit_static_impl(const mppic_config* c, const mppic_parcels* pc, double* Vs_out,
+                                 cudaStream_t st, u64* base) {
+  mppic_handle* h = nullptr;  // errors go to the creation message buffer
+  KParams<T> p;
+  memset(&p, 0, sizeof(p));
+  p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
+  p.nnode = (long long)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+  const double hs[3] = {c->dx, c->dy, c->dz};
+  for (int a = 0; a < 3; ++a) {
+    p.inv_d[a] = 1.0 / hs[a];
+    p.inv_f[a] = (float)p.inv_d[a];
+    p.inv_lo[a] = (float)(p.inv_d[a] - (double)p.inv_f[a]);
+  }
+  p.vcoef = (T)(M_PI / 6.0 * c->dscale * c->dscale * c->dscale);
+  const double vcell = c->dx * c->dy * c->dz;
+  const double mV = std::ldexp(1.0, sizeof(T) == 4 ? 48 : 96) / vcell;
+  p.mV = (T)mV;
+  u64* acc = base + 32;                         // the first 256 bytes hold the flag word
+  p.errs = reinterpret_cast<int*>(base);
+  CU(cudaMemsetAsync(base, 0, sizeof(u64) * (32 + (size_t)Words<T>::n * p.nnode), st));
+  if (pc->np > 0) {
+    k_deposit_static<T><<<blocks(pc->np, 256), 256, 0, st>>>(
+        p, static_cast<const T*>(pc->x), static_cast<const T*>(pc->y),
+        static_cast<const T*>(pc->z), static_cast<const T*>(pc->d),
+        static_cast<const T*>(pc->omega), pc->np, acc);
+    LAUNCHED();
+  }
+  k_static_out<T><<<blocks(p.nnode, 256), 256, 0, st>>>(acc, p.nnode, 1.0 / (double)p.mV, Vs_out);
+  LAUNCHED();
+  return MPPIC_OK;
+}
+
+}  // namespace
+
+extern "C" mppic_status mppic_deposit_static(const mppic_config* cfg, const mppic_parcels* parcels,
+                                             double* Vs_out, void* stream) {
+  mppic_handle* h = nullptr;
+  if (!cfg || !parcels || !Vs_out)
+    return fail(h, MPPIC_ERR_INVALID, "cfg, parcels and Vs_out must not be NULL");
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || !(cfg->dx > 0 && cfg->dy > 0 && cfg->dz > 0))
+    return fail(h, MPPIC_ERR_INVALID, "grid and spacing must be positive");
+  if (cfg->precision != 32 && cfg->precision != 64)
+    return fail(h, MPPIC_ERR_INVALID, "precision must be 32 or 64, got %d", cfg->precision);
+  const long long nnode = (long long)(cfg->nx + 1) * (cfg->ny + 1) * (cfg->nz + 1);
+  if (nnode > MPPIC_STATIC_MAX_NODES)
+    return fail(h, MPPIC_ERR_INVALID,
+                "mppic_deposit_static: %lld nodes exceed the static scratch limit of %d nodes",
+                nnode, MPPIC_STATIC_MAX_NODES);
+  if (parcels->np < 0 || parcels->np > 0x7fffffffLL)
+    return fail(h, MPPIC_ERR_INVALID, "np=%lld out of range", parcels->np);
+  if (parcels->np > 0 && (!parcels->x || !parcels->y || !parcels->z || !parcels->d || !parcels->omega))
+    return fail(h, MPPIC_ERR_INVALID, "x, y, z, d and omega must not be NULL");
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(h, MPPIC_ERR_INVALID, "device %d unsupported", dev);
+  if (!g_static_addr[dev]) {             // set-up, once per device, with the device current
+    void* addr = nullptr;
+    CU(cudaGetSymbolAddress(&addr, g_static_scratch));
+    g_static_addr[dev] = addr;
+  }
+  u64* base = static_cast<u64*>(g_static_addr[dev]);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return cfg->precision == 32 ? deposit_static_impl<float>(cfg, parcels, Vs_out, st, base)
+                              : deposit_static_impl<double>(cfg, parcels, Vs_out, st, base);
+}
