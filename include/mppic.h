@@ -75,7 +75,9 @@ typedef struct {
 /* Parcel state, structure of arrays, np entries each (caller-owned device memory).
  * x,y,z,u,v,w,d,omega are float or double per the precision. cell receives the row-major
  * cell id of each parcel's current position. Sorting permutes every array together;
- * pid (optional, may be NULL) lets the caller follow parcel identity through sorts. */
+ * pid (optional, may be NULL) lets the caller follow parcel identity through sorts.
+ * The eight value arrays must start on 16-byte boundaries (as cudaMalloc and PyTorch
+ * allocations do); calls with unaligned arrays return MPPIC_ERR_INVALID. */
 typedef struct {
   void *x, *y, *z, *u, *v, *w, *d, *omega;
   int32_t *cell;

@@ -149,6 +149,10 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   p.eg_min = (T)c.eps_g_min; p.e_wall = (T)c.e_wall; p.C = (T)c.drag_mult; p.sd = (T)c.dscale;
   p.dt = (T)c.dt; p.u_in = (T)c.u_in;
   p.vcoef = (T)(M_PI / 6.0 * c.dscale * c.dscale * c.dscale);
+  p.inv_rho_p = (T)(1.0 / c.rho_p);
+  p.kRe = (T)(c.rho_g / c.mu_g);
+  p.kD1 = (T)(c.drag_mult * 18.0 * c.mu_g / c.rho_p);
+  p.kD2 = (T)(c.drag_mult * 0.33 * c.rho_g / c.rho_p);
   // Fixed-point units: Vs in cell volumes, A and B in rho_p * cell volume per second.
   const int SV = sizeof(T) == 4 ? 48 : 96, SA = sizeof(T) == 4 ? 40 : 88;
   double mV = std::ldexp(1.0, SV) / p.vcell;
@@ -195,6 +199,11 @@ mppic_status check_parcels(mppic_handle* h, const mppic_parcels* pc) {
   if (pc->np > 0 && (!pc->x || !pc->y || !pc->z || !pc->u || !pc->v || !pc->w || !pc->d ||
                      !pc->omega))
     return fail(h, MPPIC_ERR_INVALID, "a parcel array is NULL");
+  // the brick kernels bulk-copy the parcel arrays, which needs 16-byte aligned bases
+  const void* arrays[8] = {pc->x, pc->y, pc->z, pc->u, pc->v, pc->w, pc->d, pc->omega};
+  for (int f = 0; f < 8; ++f)
+    if (((uintptr_t)arrays[f]) % 16 != 0)
+      return fail(h, MPPIC_ERR_INVALID, "parcel array %d is not 16-byte aligned", f);
   return MPPIC_OK;
 }
 
@@ -275,7 +284,7 @@ mppic_status clear_volume_accumulator(mppic_handle* h) {
 
 template <class T>
 mppic_status launch_brick(mppic_handle* h, int mode, const KParams<T>& p, PArrays<T> src,
-                          PArrays<T> dst, int* cell_out) {
+                          PArrays<T> dst, int* cell_out, long long np) {
   const size_t sm = BrickSmem<T>::bytes;
   static bool attr_set[2] = {false, false};
   if (!attr_set[mode]) {
@@ -290,10 +299,10 @@ mppic_status launch_brick(mppic_handle* h, int mode, const KParams<T>& p, PArray
   ph.launched();
   if (mode == 0)
     k_brick<T, 0><<<(unsigned)h->nbricks, BCELLS, sm, h->stream>>>(p, src, dst, nullptr,
-                                                                   h->obj_part);
+                                                                   h->obj_part, np);
   else
     k_brick<T, 1><<<(unsigned)h->nbricks, BCELLS, sm, h->stream>>>(p, src, dst, cell_out,
-                                                                   h->obj_part);
+                                                                   h->obj_part, np);
   LAUNCHED();
   return MPPIC_OK;
 }
@@ -314,7 +323,7 @@ mppic_status deposit_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_
   KParams<T> p = make_params<T>(h, gas);
   mppic_status s = clear_volume_accumulator(h);
   if (s) return s;
-  s = launch_brick<T>(h, 0, p, src, src, nullptr);
+  s = launch_brick<T>(h, 0, p, src, src, nullptr, pc->np);
   if (s) return s;
   {
     Phase ph(h, PH_FINALIZE);
@@ -342,7 +351,7 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   KParams<T> p = make_params<T>(h, gas);
   mppic_status s = clear_volume_accumulator(h);
   if (s) return s;
-  s = launch_brick<T>(h, 0, p, src, src, nullptr);   // Vs of the current positions
+  s = launch_brick<T>(h, 0, p, src, src, nullptr, pc->np);   // Vs of the current positions
   if (s) return s;
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   for (int it = 0; it < nsteps; ++it) {
@@ -357,7 +366,7 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
       k_finalize<T><<<blocks(h->nnode, 256), 256, 0, h->stream>>>(p, nullptr);
       LAUNCHED();
     }
-    s = launch_brick<T>(h, 1, p, src, dst, it == nsteps - 1 ? pc->cell : nullptr);
+    s = launch_brick<T>(h, 1, p, src, dst, it == nsteps - 1 ? pc->cell : nullptr, np);
     if (s) return s;
     src = dst;
     {
@@ -555,6 +564,7 @@ mppic_status mppic_check(mppic_handle* h) {
   int flags = 0;
   CU(cudaMemcpy(&flags, h->errs, sizeof(int), cudaMemcpyDeviceToHost));
   CU(cudaMemset(h->errs, 0, sizeof(int)));
+  if (flags & ERR_TIMEOUT) return fail(h, MPPIC_ERR_TIMEOUT, "a bulk copy wait gave up");
   if (flags & ERR_RANGE) return fail(h, MPPIC_ERR_RANGE, "a fixed-point accumulator left its range");
   if (flags & ERR_DOMAIN)
     return fail(h, MPPIC_ERR_DOMAIN, "a parcel left the box after reflection or became non-finite");

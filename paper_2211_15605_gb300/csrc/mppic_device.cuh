@@ -30,7 +30,7 @@ constexpr int BCELLS = BX * BY * BZ;             // 256 = threads per brick CTA
 constexpr int TX = BX + 1, TY = BY + 1, TZ = BZ + 1;
 constexpr int TNODES = TX * TY * TZ;             // 405 nodes per brick tile
 constexpr int NQ = 5;                            // Vs, A, Bx, By, Bz
-constexpr int ERR_DOMAIN = 1, ERR_RANGE = 2;
+constexpr int ERR_DOMAIN = 1, ERR_RANGE = 2, ERR_TIMEOUT = 4;
 
 typedef unsigned long long u64;
 
@@ -49,6 +49,9 @@ struct KParams {
   double vcell;
   T rho_g, mu_g, g[3], gp[3], rho_p, Ps, beta, eps_cp, alpha, eg_min, e_wall, C, sd, dt;
   T vcoef;                   // pi/6 * s_d^3: V = w d^3 vcoef
+  T inv_rho_p;               // 1 / rho_p
+  T kRe;                     // rho_g / mu_g (Re_m = eps_g d |s| kRe)
+  T kD1, kD2;                // C 18 mu / rho_p and C 0.33 rho_g / rho_p (drag prefactors)
   T mV, mA;                  // fixed-point multipliers (value * m = integer units)
   double inv_mV, inv_mA;
   T u_in;
@@ -225,7 +228,13 @@ struct Interp {
 };
 
 template <class T>
-__device__ __forceinline__ void interp8(const KParams<T>& p, const T* const* f, const T* const* g,
+struct Fields {
+  const T* f[5];   // eps_s, u_g x/y/z, tau
+  const T* g[3];   // grad p (used when has_g)
+};
+
+template <class T>
+__device__ __forceinline__ void interp8(const KParams<T>& p, const Fields<T> F, bool has_g,
                                         long long base, long long sx, long long sy, long long sz,
                                         const T (&xi)[3], Interp<T>& r) {
   T w[3][2];
@@ -240,21 +249,21 @@ __device__ __forceinline__ void interp8(const KParams<T>& p, const T* const* f, 
       for (int a = 0; a < 2; ++a) {
         long long n = base + a * sx + b * sy + c * sz;
         T W = (w[0][a] * w[1][b]) * w[2][c];
-        r.es += W * f[0][n];
-        r.ug[0] += W * f[1][n];
-        r.ug[1] += W * f[2][n];
-        r.ug[2] += W * f[3][n];
-        T tau = f[4][n];
+        r.es += W * F.f[0][n];
+        r.ug[0] += W * F.f[1][n];
+        r.ug[1] += W * F.f[2][n];
+        r.ug[2] += W * F.f[3][n];
+        T tau = F.f[4][n];
         r.gt[0] += ((a ? p.invh[0] : -p.invh[0]) * (w[1][b] * w[2][c])) * tau;
         r.gt[1] += ((b ? p.invh[1] : -p.invh[1]) * (w[0][a] * w[2][c])) * tau;
         r.gt[2] += ((c ? p.invh[2] : -p.invh[2]) * (w[0][a] * w[1][b])) * tau;
-        if (g) {
-          r.gp[0] += W * g[0][n];
-          r.gp[1] += W * g[1][n];
-          r.gp[2] += W * g[2][n];
+        if (has_g) {
+          r.gp[0] += W * F.g[0][n];
+          r.gp[1] += W * F.g[1][n];
+          r.gp[2] += W * F.g[2][n];
         }
       }
-  if (!g) { r.gp[0] = p.gp[0]; r.gp[1] = p.gp[1]; r.gp[2] = p.gp[2]; }
+  if (!has_g) { r.gp[0] = p.gp[0]; r.gp[1] = p.gp[1]; r.gp[2] = p.gp[2]; }
 }
 
 __device__ __forceinline__ float tpow(float a, float b) { return powf(a, b); }
@@ -460,48 +469,145 @@ __global__ void k_gather(PArrays<T> src, PArrays<T> dst, const uint32_t* __restr
 // ------------------------------------------------------------ brick CTA --
 
 template <class T> struct Chunk;                          // parcels per CTA chunk
-template <> struct Chunk<float> { static constexpr int n = 1024; };
-template <> struct Chunk<double> { static constexpr int n = 384; };
+template <> struct Chunk<float> { static constexpr int n = 512; };
+template <> struct Chunk<double> { static constexpr int n = 256; };
 
-// Shared-memory layout of the brick kernels.
+constexpr size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Shared-memory layout of the brick kernels (every section 128-byte aligned; the staging
+// rows must be 16-byte aligned for the bulk copies).
 template <class T>
 struct BrickSmem {
   static constexpr int W = Words<T>::n;
   static constexpr int NC = Chunk<T>::n;
-  // node fields tile: 5 fields (+3 grad p) x TNODES
-  static constexpr size_t fld_bytes = sizeof(T) * 8 * TNODES;
-  // fixed-point tile: NQ x W x TNODES words
-  static constexpr size_t acc_bytes = sizeof(u64) * NQ * W * TNODES;
-  // records: f, u[3], xi_old[3], V, xi_new[3] (11 T) + old and new cell (2 int)
-  static constexpr size_t rec_bytes = NC * (11 * sizeof(T) + 2 * sizeof(int));
-  static constexpr size_t bytes = fld_bytes + acc_bytes + rec_bytes;
+  static constexpr int SPAD = NC + 8;                                    // staging row length
+  static constexpr size_t fld = 0;                                       // [TNODES][8] T (AoS)
+  static constexpr size_t acc = rup(fld + sizeof(T) * 8 * TNODES, 128);  // [NQ][TNODES] T
+  static constexpr size_t stage = rup(acc + sizeof(T) * NQ * TNODES, 128);  // [2][8][SPAD] T
+  static constexpr size_t rec = rup(stage + sizeof(T) * 2 * 8 * SPAD, 128);
+  // records: f, xi_old[3], xi_new[3] (7 T), old and new cell (2 int), local key (int)
+  static constexpr size_t cells = rup(rec + sizeof(T) * 7 * NC + sizeof(int) * 3 * NC, 128);
+  // list of records not in their sorted cell [NC], and each cell's record range in the
+  // chunk [2][BCELLS]
+  static constexpr size_t misc = rup(cells + sizeof(int) * (NC + 2 * BCELLS), 128);
+  // 2 mbarriers (16 B) + 16 ints: abort flag, drift-list length, first and last cell of
+  // the chunk, per-warp drift counts
+  static constexpr size_t bytes = misc + 16 + 16 * sizeof(int);
 };
 
-// Adds the fixed-point contributions of one parcel (values q at the 8 corners of cell
-// (i,j,k) with in-cell coordinates xi) to the shared tile where the node is inside the
-// brick tile, else to the global accumulators. Used for parcels outside their sorted cell.
+// ---- bulk-copy staging (cp.async.bulk with an mbarrier, bounded waits)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* m) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(m)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Waits for the given phase parity; gives up after a bounded number of polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
+  const uint32_t a = smem_addr(m);
+  for (int it = 0; it < (1 << 16); ++it) {
+    uint32_t done;
+    // the suspend-time hint (ns) lets the thread sleep in the instruction instead of polling
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(20000u)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(m))
+      : "memory");
+}
+
+// The staged element range of a chunk [c0, c0+cn): [c0 & ~3, end) is copied in bulk, where
+// end is c0+cn rounded up to 4 elements but not past the last full group of 4 of the
+// array (np), so no byte beyond the caller's array is read. Elements from end to c0+cn
+// are loaded with plain loads.
+__device__ __forceinline__ long long bulk_end(long long c0, int cn, long long np) {
+  long long s0 = c0 & ~3LL;
+  long long e = (c0 + cn + 3) & ~3LL;
+  long long lim = np & ~3LL;
+  if (e > lim) e = lim;
+  if (e < s0) e = s0;
+  return e;
+}
+
+template <class T>
+__device__ void issue_chunk(const PArrays<T>& src, long long c0, int cn, long long np, T* stage_buf,
+                            uint64_t* m) {
+  constexpr int SPAD = BrickSmem<T>::SPAD;
+  const long long s0 = c0 & ~3LL;
+  const uint32_t bytes = (uint32_t)((bulk_end(c0, cn, np) - s0) * sizeof(T));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect(m, 8u * bytes);
+  if (bytes)
+    for (int f = 0; f < 8; ++f) bulk_g2s(stage_buf + f * SPAD, src.a[f] + s0, bytes, m);
+}
+
+// ---- math of the step: full precision in the FP64 form, CUDA's fast intrinsics in FP32.
+__device__ __forceinline__ float fpow(float a, float b) { return __powf(a, b); }
+__device__ __forceinline__ double fpow(double a, double b) { return pow(a, b); }
+__device__ __forceinline__ float frcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double frcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float fsqrt(float a) { return a > 0.0f ? a * rsqrtf(a) : 0.0f; }
+__device__ __forceinline__ double fsqrt(double a) { return sqrt(a); }
+
+// Wen-Yu drag as an acceleration coefficient (same closure as wen_yu, in the form
+// D = C 18 mu (1 + 0.15 Re_m^0.687) eps_g^-2.65 / (d^2 rho_p) below Re_m = 1000 and
+// D = C 0.33 rho_g |s| eps_g^-1.65 / (d rho_p) above).
+template <class T>
+__device__ __forceinline__ T wen_yu_fast(const KParams<T>& p, T d, T es, const T (&s)[3]) {
+  T eg = tmax(T(1) - es, p.eg_min);
+  T de = p.sd * d;
+  T inv_de = frcp(de);
+  T smag = fsqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+  T rem = eg * de * smag * p.kRe;
+  T e165 = fpow(eg, T(-1.65));
+  if (rem < T(1000))
+    return p.kD1 * (T(1) + T(0.15) * fpow(rem, T(0.687))) * e165 * frcp(eg) * (inv_de * inv_de);
+  return p.kD2 * smag * e165 * inv_de;
+}
+
+// Adds the fixed-point contributions of one parcel (values at the 8 corners of cell (i,j,k)
+// with in-cell coordinates xi) straight to the global accumulators. Used for parcels whose
+// cell is not their sorted cell (they drifted since the last sort, or moved this step).
 template <class T, int NV>
-__device__ void scatter_parcel(const KParams<T>& p, u64* tile, int bi0, int bj0, int bk0, int i,
-                               int j, int k, const T (&xi)[3], const T (&vals)[NV], int q0) {
+__device__ __noinline__ void scatter_global(const KParams<T>& p, int cell, T x0, T x1, T x2, T v0,
+                                            T v1, T v2, T v3) {
   constexpr int W = Words<T>::n;
-  T w[3][2];
-  for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - xi[a]; w[a][1] = xi[a]; }
+  int i, j, k;
+  decode_cell(p, cell, i, j, k);
+  const T vals[4] = {v0, v1, v2, v3};
+  const T w[3][2] = {{T(1) - x0, x0}, {T(1) - x1, x1}, {T(1) - x2, x2}};
+  const int q0 = NV == 1 ? 0 : 1;
   for (int c = 0; c < 2; ++c)
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
         T Wq = (w[0][a] * w[1][b]) * w[2][c];
-        int ti = i + a - bi0, tj = j + b - bj0, tk = k + c - bk0;
-        bool in_tile = ti >= 0 && ti < TX && tj >= 0 && tj < TY && tk >= 0 && tk < TZ;
         long long gn = node_id(p, i + a, j + b, k + c);
-        int tn = ti + TX * (tj + TY * tk);
+#pragma unroll
         for (int v = 0; v < NV; ++v) {
           int q = q0 + v;
           u64 fx[W];
           to_fixed(vals[v] * Wq, q == 0 ? p.mV : p.mA, fx, p.errs);
-          if (in_tile)
-            acc_add(tile + (q * W) * TNODES + tn, TNODES, fx);
-          else
-            acc_add(p.acc + (long long)(q * W) * p.nnode + gn, p.nnode, fx);
+          acc_add(p.acc + (long long)(q * W) * p.nnode + gn, p.nnode, fx);
         }
       }
 }
@@ -523,31 +629,113 @@ __device__ void block_sum3(T a, T b, T c, T* sm, double* out) {
   if (t == 0) { out[0] = (double)sm[0]; out[1] = (double)sm[BCELLS]; out[2] = (double)sm[2 * BCELLS]; }
 }
 
-// The brick kernel. MODE 0: deposit the solids volume of the current positions.
-// MODE 1: one full step for the parcels of the brick (interp, drag, drag sums, objectives,
-// push, walls, re-bin) with the solids volume of the new positions deposited for the next
-// step. src/dst may be the same arrays; if not, the read-only arrays are copied too.
+// Node values of corner n of the AoS field tile: eps_s, u_g[3], tau, grad p[3].
+__device__ __forceinline__ void tile_node(const float* t, int n, float (&v)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(t + 8 * n);
+  const float4 b = *reinterpret_cast<const float4*>(t + 8 * n + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void tile_node(const double* t, int n, double (&v)[8]) {
+  for (int f = 0; f < 8; f += 2) {
+    const double2 a = *reinterpret_cast<const double2*>(t + 8 * n + f);
+    v[f] = a.x; v[f + 1] = a.y;
+  }
+}
+
+// Interpolation at one parcel from the brick's AoS field tile (corner (0,0,0) at tile node
+// base). The gradient of the trilinear interpolant of tau is formed from differences across
+// the cell faces: d/dx = (1/dx) sum_{b,c} (tau_1bc - tau_0bc) w_y,b w_z,c, and likewise.
+template <class T>
+__device__ __forceinline__ void interp_tile(const KParams<T>& p, const T* t, int base,
+                                            const T (&xi)[3], Interp<T>& r) {
+  T w[3][2];
+  for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - xi[a]; w[a][1] = xi[a]; }
+  T tau[8];
+  r.es = 0;
+  for (int a = 0; a < 3; ++a) { r.ug[a] = 0; r.gp[a] = 0; }
+  const bool gpf = p.has_gp != 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
+    T v[8];
+    tile_node(t, base + a + TX * (b + TY * c), v);
+    const T W = (w[0][a] * w[1][b]) * w[2][c];
+    r.es += W * v[0];
+    r.ug[0] += W * v[1];
+    r.ug[1] += W * v[2];
+    r.ug[2] += W * v[3];
+    tau[q] = v[4];
+    if (gpf) {
+      r.gp[0] += W * v[5];
+      r.gp[1] += W * v[6];
+      r.gp[2] += W * v[7];
+    }
+  }
+  if (!gpf) { r.gp[0] = p.gp[0]; r.gp[1] = p.gp[1]; r.gp[2] = p.gp[2]; }
+  T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int u0 = q & 1, u1 = q >> 1;
+    // x-faces: corners (0,u0,u1) and (1,u0,u1); y-faces: (u0,0,u1), (u0,1,u1); z: (u0,u1,0), (u0,u1,1)
+    gx += (tau[1 + 2 * u0 + 4 * u1] - tau[2 * u0 + 4 * u1]) * (w[1][u0] * w[2][u1]);
+    gy += (tau[u0 + 2 + 4 * u1] - tau[u0 + 4 * u1]) * (w[0][u0] * w[2][u1]);
+    gz += (tau[u0 + 2 * u1 + 4] - tau[u0 + 2 * u1]) * (w[0][u0] * w[1][u1]);
+  }
+  r.gt[0] = gx * p.invh[0];
+  r.gt[1] = gy * p.invh[1];
+  r.gt[2] = gz * p.invh[2];
+}
+
+// The brick kernel. One CTA owns the parcels of one brick (its range of the sorted order).
+// MODE 0: deposit the solids volume of the current positions.
+// MODE 1: one full step for those parcels (interp, drag, drag sums, objectives, push,
+// walls, re-bin), depositing the solids volume of the new positions for the next step.
+// src/dst may be the same arrays; if not, the read-only arrays are copied too.
+//
+// Per chunk of NC parcels: the 8 parcel arrays are bulk-copied into shared memory (the
+// next chunk's copy is in flight while this one is processed); phase A runs one parcel per
+// thread and leaves a record; phase B, one thread per cell, sums the records of its cell in
+// registers and adds the sums to a shared node tile in 8 corner phases separated by
+// barriers, so no two threads touch a node in the same phase and the order is fixed.
+// Records whose cell is not their sorted cell go to the global accumulators in exact
+// fixed point. At the end of the brick the tile is converted to fixed point and added to
+// the global accumulators.
+template <class T> struct Occupancy;
+template <> struct Occupancy<float> { static constexpr int ctas = 2; };
+template <> struct Occupancy<double> { static constexpr int ctas = 2; };
+
 template <class T, int MODE>
-__global__ void __launch_bounds__(BCELLS, 2)
+__global__ void __launch_bounds__(BCELLS, Occupancy<T>::ctas)
 k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out,
-        double* __restrict__ obj_part) {
-  constexpr int W = Words<T>::n;
-  constexpr int NC = Chunk<T>::n;
-  extern __shared__ __align__(16) unsigned char smem[];
-  T* sf = reinterpret_cast<T*>(smem);                                        // [8][TNODES]
-  u64* tile = reinterpret_cast<u64*>(smem + BrickSmem<T>::fld_bytes);       // [NQ*W][TNODES]
-  unsigned char* recb = smem + BrickSmem<T>::fld_bytes + BrickSmem<T>::acc_bytes;
-  T* rf = reinterpret_cast<T*>(recb);            // f
-  T* ru = rf + NC;                               // u_old [3][NC]
-  T* rxo = ru + 3 * NC;                          // xi_old [3][NC]
-  T* rV = rxo + 3 * NC;                          // V
-  T* rxn = rV + NC;                              // xi_new [3][NC]
+        double* __restrict__ obj_part, long long np) {
+  typedef BrickSmem<T> S;
+  constexpr int W = S::W;
+  constexpr int NC = S::NC;
+  constexpr int SPAD = S::SPAD;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* sf = reinterpret_cast<T*>(smem + S::fld);          // [TNODES][8]
+  T* tile = reinterpret_cast<T*>(smem + S::acc);        // [NQ][TNODES]
+  T* stage = reinterpret_cast<T*>(smem + S::stage);
+  T* rf = reinterpret_cast<T*>(smem + S::rec);
+  T* rxo = rf + NC;                              // [3][NC]
+  T* rxn = rxo + 3 * NC;                         // [3][NC]
   int* rco = reinterpret_cast<int*>(rxn + 3 * NC);
   int* rcn = rco + NC;
+  int* rkey = rcn + NC;                          // local cell of the current position, or BCELLS
+  int* drift = reinterpret_cast<int*>(smem + S::cells);  // [NC] records not in their sorted cell
+  int* cr0 = drift + NC;                         // [BCELLS] chunk record range of each sorted cell
+  int* cr1 = cr0 + BCELLS;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::misc);
+  int* sflag = reinterpret_cast<int*>(smem + S::misc + 16);
+  // sflag: [0] abort, [1] drift-list length, [2] first cell, [3] last cell, [4..11] per-warp drift counts
 
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const unsigned lanes_below = (1u << lane) - 1u;
   const long long b = blockIdx.x;
-  const int bi = (int)(b % p.nbx), bj = (int)((b / p.nbx) % p.nby), bk = (int)(b / ((long long)p.nbx * p.nby));
+  const unsigned bu = blockIdx.x;
+  const int bi = (int)(bu % (unsigned)p.nbx), bj = (int)((bu / (unsigned)p.nbx) % (unsigned)p.nby),
+            bk = (int)(bu / ((unsigned)p.nbx * (unsigned)p.nby));
   const int bi0 = bi * BX, bj0 = bj * BY, bk0 = bk * BZ;
   const long long kbase = b * BCELLS;
   const int pstart = p.cstart[kbase], pend = p.cstart[kbase + BCELLS];
@@ -557,85 +745,110 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
     return;
   }
 
-  // this thread's cell in the brick
-  const int li = tid % BX, lj = (tid / BX) % BY, lk = tid / (BX * BY);
-  const int gi = bi0 + li, gj = bj0 + lj, gk = bk0 + lk;
-  const bool cell_ok = gi < p.nx && gj < p.ny && gk < p.nz;
-  const int mycell = cell_ok ? cell_id(p, gi, gj, gk) : -1;
-  const int cs = p.cstart[kbase + tid], ce = p.cstart[kbase + tid + 1];
-  const int tbase = li + TX * (lj + TY * lk);     // tile node of corner (0,0,0)
-
-  // zero the accumulator tile; stage the node-field tile (MODE 1)
-  for (int e = tid; e < NQ * W * TNODES; e += BCELLS) tile[e] = 0;
+  for (int e = tid; e < NQ * TNODES; e += BCELLS) tile[e] = 0;
   if (MODE == 1) {
-    const int nf = p.has_gp ? 8 : 5;
-    for (int e = tid; e < nf * TNODES; e += BCELLS) {
-      int f = e / TNODES, tn = e % TNODES;
+    for (int e = tid; e < 8 * TNODES; e += BCELLS) {
+      int tn = e >> 3, f = e & 7;
       int ti = tn % TX, tj = (tn / TX) % TY, tk = tn / (TX * TY);
       int i = bi0 + ti, j = bj0 + tj, k = bk0 + tk;
       T v = 0;
-      if (i <= p.nx && j <= p.ny && k <= p.nz) {
+      if (i <= p.nx && j <= p.ny && k <= p.nz && (f < 5 || p.has_gp)) {
         long long n = node_id(p, i, j, k);
         v = f < 5 ? p.fld[f][n] : p.gpf[f - 5][n];
       }
       sf[e] = v;
     }
   }
+  if (tid == 0) {
+    mbar_init(&mbar[0]);
+    mbar_init(&mbar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sflag[0] = 0;
+  }
   __syncthreads();
 
-  const T* tf[5] = {sf, sf + TNODES, sf + 2 * TNODES, sf + 3 * TNODES, sf + 4 * TNODES};
-  const T* tg[3] = {sf + 5 * TNODES, sf + 6 * TNODES, sf + 7 * TNODES};
+  Fields<T> FG;
+  for (int f = 0; f < 5; ++f) FG.f[f] = p.fld[f];
+  for (int a = 0; a < 3; ++a) FG.g[a] = p.gpf[a];
   const long long sxg = 1, syg = p.nx + 1, szg = (long long)(p.nx + 1) * (p.ny + 1);
   T o_dp = 0, o_hn = 0, o_vs = 0;
+  const int nchunks = (pend - pstart + NC - 1) / NC;
+  if (tid == 0) issue_chunk(src, pstart, min(NC, pend - pstart), np, stage, &mbar[0]);
 
-  for (int c0 = pstart; c0 < pend; c0 += NC) {
-    const int cn = min(NC, pend - c0);
+  for (int kc = 0; kc < nchunks; ++kc) {
+    const int buf = kc & 1;
+    const long long c0 = (long long)pstart + (long long)kc * NC;
+    const int cn = (int)min((long long)NC, (long long)pend - c0);
+    const long long s0 = c0 & ~3LL;
+    T* sb = stage + buf * 8 * SPAD;
+    if (tid == 0 && kc + 1 < nchunks) {
+      const long long c1 = c0 + NC;
+      issue_chunk(src, c1, (int)min((long long)NC, (long long)pend - c1), np,
+                  stage + (buf ^ 1) * 8 * SPAD, &mbar[buf ^ 1]);
+    }
+    // one thread waits for the chunk's bulk copies; the others sleep at the barrier below
+    if (tid == 0 && !mbar_wait(&mbar[buf], (uint32_t)((kc >> 1) & 1))) {
+      atomicOr(p.errs, ERR_TIMEOUT);
+      sflag[0] = 1;
+    }
+    {  // ragged tail beyond the last full group of 4 of the arrays
+      const long long e = bulk_end(c0, cn, np);
+      const long long t0 = e > c0 ? e : c0;
+      const int ntail = (int)(c0 + cn - t0);
+      for (int t = tid; t < 8 * ntail; t += BCELLS) {
+        const int f = t / ntail;
+        const long long q = t0 + (t % ntail);
+        sb[f * SPAD + (int)(q - s0)] = src.a[f][q];
+      }
+    }
+    __syncthreads();
+    if (sflag[0]) {             // a bulk copy never completed: drain what was issued and leave
+      if (tid == 0 && kc + 1 < nchunks) mbar_wait(&mbar[buf ^ 1], (uint32_t)(((kc + 1) >> 1) & 1));
+      return;
+    }
     // ---- phase A: one parcel per thread
     for (int r = tid; r < cn; r += BCELLS) {
-      const long long q = (long long)c0 + r;
-      T x = src.a[0][q], y = src.a[1][q], z = src.a[2][q];
-      T d = src.a[6][q], om = src.a[7][q];
-      T V = om * (d * d * d) * p.vcoef;
+      const long long q = c0 + r;
+      const int si = (int)(q - s0);
+      T x = sb[si], y = sb[SPAD + si], z = sb[2 * SPAD + si];
       Cell3<T> c;
       bin3(p, x, y, z, c);
       const int oldcell = cell_id(p, c.i, c.j, c.k);
+      const int ti = c.i - bi0, tj = c.j - bj0, tk = c.k - bk0;
+      const bool inb = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
+      rkey[r] = inb ? ti + BX * (tj + BY * tk) : BCELLS;
       if (MODE == 0) {
-        rV[r] = V;
         rxn[r] = c.xi[0]; rxn[NC + r] = c.xi[1]; rxn[2 * NC + r] = c.xi[2];
         rcn[r] = oldcell;
         continue;
       }
-      T u = src.a[3][q], v = src.a[4][q], w = src.a[5][q];
-      // interpolation: from the tile if the cell is in this brick, else from global memory
+      T u = sb[3 * SPAD + si], v = sb[4 * SPAD + si], w = sb[5 * SPAD + si];
+      T d = sb[6 * SPAD + si], om = sb[7 * SPAD + si];
+      T V = om * (d * d * d) * p.vcoef;
       Interp<T> I;
-      int ti = c.i - bi0, tj = c.j - bj0, tk = c.k - bk0;
-      if (ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ) {
-        interp8(p, tf, p.has_gp ? tg : nullptr, ti + TX * (tj + TY * tk), 1, TX, TX * TY, c.xi, I);
-      } else {
-        const T* gf[5] = {p.fld[0], p.fld[1], p.fld[2], p.fld[3], p.fld[4]};
-        interp8(p, gf, p.has_gp ? p.gpf : nullptr, node_id(p, c.i, c.j, c.k), sxg, syg, szg, c.xi, I);
-      }
+      if (inb)
+        interp_tile(p, sf, ti + TX * (tj + TY * tk), c.xi, I);
+      else
+        interp8(p, FG, p.has_gp != 0, node_id(p, c.i, c.j, c.k), sxg, syg, szg, c.xi, I);
       T up[3] = {u, v, w};
       T s[3] = {I.ug[0] - u, I.ug[1] - v, I.ug[2] - w};
-      T D = wen_yu(p, d, I.es, s);
+      T D = wen_yu_fast(p, d, I.es, s);
       T f = p.rho_p * V * D;
       o_dp += f * s[2];
       o_hn += V * z;
       o_vs += V;
       rf[r] = f;
-      ru[r] = u; ru[NC + r] = v; ru[2 * NC + r] = w;
       rxo[r] = c.xi[0]; rxo[NC + r] = c.xi[1]; rxo[2 * NC + r] = c.xi[2];
-      rV[r] = V;
       rco[r] = oldcell;
       // semi-implicit push (Eq. 4 / (eps_P rho_P), drag implicit), Eq. 3, specular walls
       T pos[3] = {x, y, z};
-      const T den = T(1) + p.dt * D;
+      const T inv_den = frcp(T(1) + p.dt * D);
+      const T inv_esr = I.es > T(1e-12) ? frcp(I.es * p.rho_p) : T(0);
       bool bad = false;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        T acc = D * I.ug[a] + p.g[a] - I.gp[a] / p.rho_p;
-        if (I.es > T(1e-12)) acc = acc - I.gt[a] / (I.es * p.rho_p);
-        T un = (up[a] + p.dt * acc) / den;
+        T acc = D * I.ug[a] + p.g[a] - I.gp[a] * p.inv_rho_p - I.gt[a] * inv_esr;
+        T un = (up[a] + p.dt * acc) * inv_den;
         T xn = pos[a] + p.dt * un;
         if (xn < T(0)) { xn = -xn; un = -p.e_wall * un; }
         else if (xn > p.L[a]) { xn = T(2) * p.L[a] - xn; un = -p.e_wall * un; }
@@ -658,85 +871,173 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
       if (cell_out) cell_out[q] = newcell;
     }
     __syncthreads();
-    // ---- phase B: one thread per cell sums the records of its sorted range
-    const int r0 = max(cs, c0) - c0, r1 = min(ce, c0 + cn) - c0;
-    if (r0 < r1) {
-      T aV[8], aA[8], aB[3][8];
+    // ---- grouping: records are in sorted-cell order; those whose current cell is not their
+    // sorted cell (drift since the last sort) are listed, in record order, for phase B
+    {
+      const int r0c = (int)(max((long long)p.cstart[kbase + tid], c0) - c0);
+      const int r1c = (int)(min((long long)p.cstart[kbase + tid + 1], c0 + cn) - c0);
+      cr0[tid] = r0c;
+      cr1[tid] = r1c < r0c ? r0c : r1c;
+    }
+    if (tid == 0) { sflag[2] = BCELLS; sflag[3] = -1; }
+    __syncthreads();
+    int ndrift = 0;
+    {
+      // thread t marks record t, t+256: drifted if its key is not the cell whose range holds it
+      const int seg = (NC + 7) / 8;
+      const int wlo = warp * seg, whi = min(cn, wlo + seg);
+      int wcount = 0, kmin = BCELLS, kmax = -1;
+      for (int rb = wlo; rb < whi; rb += 32) {
+        const int r = rb + lane;
+        bool dr = false;
+        if (r < whi) {
+          const int key = rkey[r];
+          dr = key == BCELLS || !(cr0[key] <= r && r < cr1[key]);
+          if (key < BCELLS) { kmin = min(kmin, key); kmax = max(kmax, key); }
+        }
+        wcount += __popc(__ballot_sync(0xffffffffu, dr));
+      }
+      kmin = __reduce_min_sync(0xffffffffu, kmin);
+      kmax = __reduce_max_sync(0xffffffffu, kmax);
+      if (lane == 0) {
+        sflag[4 + warp] = wcount;
+        atomicMin(&sflag[2], kmin);
+        atomicMax(&sflag[3], kmax);
+      }
+      __syncthreads();
+      int base = 0;
+      for (int w = 0; w < warp; ++w) base += sflag[4 + w];
+      for (int rb = wlo; rb < whi; rb += 32) {
+        const int r = rb + lane;
+        bool dr = false;
+        if (r < whi) {
+          const int key = rkey[r];
+          dr = key == BCELLS || !(cr0[key] <= r && r < cr1[key]);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, dr);
+        if (dr) drift[base + __popc(bal & lanes_below)] = r;
+        base += __popc(bal);
+      }
+      if (warp == 7 && lane == 0) sflag[1] = base;
+      __syncthreads();
+      ndrift = sflag[1];
+    }
+    // ---- phase B: G consecutive lanes per cell of [la, lb] sum its records in registers:
+    // the records of its sorted range still in it, then the drifted records now in it
+    const int la = sflag[2], lb = sflag[3];
+    const int nocc = lb >= la ? lb - la + 1 : 0;
+    int G = 1;
+    while (G < 8 && 2 * G * nocc <= BCELLS) G *= 2;
+    const int ci = tid / G, sub = tid % G;
+    T aV[8], aA[8], aB[3][8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) { aV[q] = 0; aA[q] = 0; aB[0][q] = 0; aB[1][q] = 0; aB[2][q] = 0; }
-      for (int r = r0; r < r1; ++r) {
+    for (int q = 0; q < 8; ++q) { aV[q] = 0; aA[q] = 0; aB[0][q] = 0; aB[1][q] = 0; aB[2][q] = 0; }
+    int l = -1;
+    if (ci < nocc) {
+      l = la + ci;
+      const int lli = l % BX, llj = (l / BX) % BY, llk = l / (BX * BY);
+      const int gcell = cell_id(p, bi0 + lli, bj0 + llj, bk0 + llk);
+      const int rs0 = cr0[l], rs1 = cr1[l];
+      const int nown = rs1 - rs0;
+      // own range first (skipping records that drifted away), then the drift list
+      for (int j = sub; j < nown + ndrift; j += G) {
+        const int r = j < nown ? rs0 + j : drift[j - nown];
+        if (rkey[r] != l) continue;
+        const int si = (int)(c0 + r - s0);
         if (MODE == 1) {
-          T xo[3] = {rxo[r], rxo[NC + r], rxo[2 * NC + r]};
-          T fr = rf[r];
-          T fu[3] = {fr * ru[r], fr * ru[NC + r], fr * ru[2 * NC + r]};
-          int co = rco[r];
-          if (co == mycell) {
-            T w[3][2];
-            for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - xo[a]; w[a][1] = xo[a]; }
+          const T xo[3] = {rxo[r], rxo[NC + r], rxo[2 * NC + r]};
+          const T fr = rf[r];
+          const T fu[3] = {fr * sb[3 * SPAD + si], fr * sb[4 * SPAD + si], fr * sb[5 * SPAD + si]};
+          T w[3][2];
+          for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - xo[a]; w[a][1] = xo[a]; }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              T Wq = (w[0][q & 1] * w[1][(q >> 1) & 1]) * w[2][q >> 2];
-              aA[q] += fr * Wq;
-              aB[0][q] += fu[0] * Wq;
-              aB[1][q] += fu[1] * Wq;
-              aB[2][q] += fu[2] * Wq;
-            }
-          } else {
-            int i, j, k;
-            decode_cell(p, co, i, j, k);
-            T vals[4] = {fr, fu[0], fu[1], fu[2]};
-            scatter_parcel<T, 4>(p, tile, bi0, bj0, bk0, i, j, k, xo, vals, 1);
+          for (int q = 0; q < 8; ++q) {
+            const T Wq = (w[0][q & 1] * w[1][(q >> 1) & 1]) * w[2][q >> 2];
+            aA[q] += fr * Wq;
+            aB[0][q] += fu[0] * Wq;
+            aB[1][q] += fu[1] * Wq;
+            aB[2][q] += fu[2] * Wq;
           }
         }
-        T xn[3] = {rxn[r], rxn[NC + r], rxn[2 * NC + r]};
-        T Vr = rV[r];
-        int cnr = rcn[r];
-        if (cnr == mycell) {
+        const T xn[3] = {rxn[r], rxn[NC + r], rxn[2 * NC + r]};
+        const T dr = sb[6 * SPAD + si];
+        const T Vr[1] = {sb[7 * SPAD + si] * (dr * dr * dr) * p.vcoef};
+        const int cnr = rcn[r];
+        if (cnr == gcell) {
           T w[3][2];
           for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - xn[a]; w[a][1] = xn[a]; }
 #pragma unroll
-          for (int q = 0; q < 8; ++q) aV[q] += Vr * ((w[0][q & 1] * w[1][(q >> 1) & 1]) * w[2][q >> 2]);
+          for (int q = 0; q < 8; ++q) aV[q] += Vr[0] * ((w[0][q & 1] * w[1][(q >> 1) & 1]) * w[2][q >> 2]);
         } else {
-          int i, j, k;
-          decode_cell(p, cnr, i, j, k);
-          T vals[1] = {Vr};
-          scatter_parcel<T, 1>(p, tile, bi0, bj0, bk0, i, j, k, xn, vals, 0);
+          scatter_global<T, 1>(p, cnr, xn[0], xn[1], xn[2], Vr[0], T(0), T(0), T(0));
         }
       }
-      // per-cell sums -> fixed point -> shared tile (corner order: no two threads of an
-      // instruction touch the same node)
+    }
+    // combine the G partial sums of a cell (consecutive lanes of one warp; in warps that
+    // hold an occupied cell every lane takes part)
+    const bool warp_busy = (warp * 32) / G < nocc;
+    for (int o = 1; warp_busy && o < G; o <<= 1) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const int tn = tbase + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2));
-        u64 fx[W];
-        to_fixed(aV[q], p.mV, fx, p.errs);
-        acc_add(tile + 0 * W * TNODES + tn, TNODES, fx);
+        aV[q] += __shfl_xor_sync(0xffffffffu, aV[q], o);
         if (MODE == 1) {
-          to_fixed(aA[q], p.mA, fx, p.errs);
-          acc_add(tile + 1 * W * TNODES + tn, TNODES, fx);
-          for (int a = 0; a < 3; ++a) {
-            to_fixed(aB[a][q], p.mA, fx, p.errs);
-            acc_add(tile + (2 + a) * W * TNODES + tn, TNODES, fx);
-          }
+          aA[q] += __shfl_xor_sync(0xffffffffu, aA[q], o);
+          aB[0][q] += __shfl_xor_sync(0xffffffffu, aB[0][q], o);
+          aB[1][q] += __shfl_xor_sync(0xffffffffu, aB[1][q], o);
+          aB[2][q] += __shfl_xor_sync(0xffffffffu, aB[2][q], o);
+        }
+      }
+    }
+    // records whose current cell is outside the brick: straight to the global accumulators
+    for (int j = tid; j < ndrift; j += BCELLS) {
+      const int r = drift[j];
+      if (rkey[r] != BCELLS) continue;
+      const int si = (int)(c0 + r - s0);
+      if (MODE == 1) {
+        const T fr = rf[r];
+        scatter_global<T, 4>(p, rco[r], rxo[r], rxo[NC + r], rxo[2 * NC + r], fr,
+                             fr * sb[3 * SPAD + si], fr * sb[4 * SPAD + si], fr * sb[5 * SPAD + si]);
+      }
+      const T dr = sb[6 * SPAD + si];
+      scatter_global<T, 1>(p, rcn[r], rxn[r], rxn[NC + r], rxn[2 * NC + r],
+                           sb[7 * SPAD + si] * (dr * dr * dr) * p.vcoef, T(0), T(0), T(0));
+    }
+    // per-cell sums into the shared tile, one corner per phase: in a phase no two cells
+    // touch the same node, so plain adds in a fixed order are deterministic
+    const bool lead = ci < nocc && sub == 0;
+    const int tbase = lead ? (l % BX) + TX * (((l / BX) % BY) + TY * (l / (BX * BY))) : 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      __syncthreads();
+      if (lead) {
+        const int tn = tbase + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2));
+        tile[tn] += aV[q];
+        if (MODE == 1) {
+          tile[TNODES + tn] += aA[q];
+          tile[2 * TNODES + tn] += aB[0][q];
+          tile[3 * TNODES + tn] += aB[1][q];
+          tile[4 * TNODES + tn] += aB[2][q];
         }
       }
     }
     __syncthreads();
   }
-  // ---- flush the tile to the global accumulators
+  // ---- the tile, in exact fixed point, to the global accumulators
   const int nq = MODE == 1 ? NQ : 1;
   for (int e = tid; e < nq * TNODES; e += BCELLS) {
     int q = e / TNODES, tn = e % TNODES;
     int ti = tn % TX, tj = (tn / TX) % TY, tk = tn / (TX * TY);
     int i = bi0 + ti, j = bj0 + tj, k = bk0 + tk;
     if (i > p.nx || j > p.ny || k > p.nz) continue;
+    T v = tile[e];
+    if (v == T(0)) continue;
     u64 fx[W];
-    for (int w = 0; w < W; ++w) fx[w] = tile[(q * W + w) * TNODES + tn];
+    to_fixed(v, q == 0 ? p.mV : p.mA, fx, p.errs);
     acc_add(p.acc + (long long)(q * W) * p.nnode + node_id(p, i, j, k), p.nnode, fx);
   }
   if (MODE == 1) {
     __syncthreads();
-    block_sum3(o_dp, o_hn, o_vs, reinterpret_cast<T*>(recb), obj_part + 3 * b);
+    block_sum3(o_dp, o_hn, o_vs, reinterpret_cast<T*>(smem + S::rec), obj_part + 3 * b);
   }
 }
 
@@ -802,9 +1103,11 @@ __global__ void k_interp_out(KParams<T> p, const T* __restrict__ x, const T* __r
   if (q >= np) return;
   Cell3<T> c;
   bin3(p, x[q], y[q], z[q], c);
-  const T* gf[5] = {p.fld[0], p.fld[1], p.fld[2], p.fld[3], p.fld[4]};
+  Fields<T> FG;
+  for (int f = 0; f < 5; ++f) FG.f[f] = p.fld[f];
+  for (int a = 0; a < 3; ++a) FG.g[a] = p.gpf[a];
   Interp<T> I;
-  interp8(p, gf, p.has_gp ? p.gpf : nullptr, node_id(p, c.i, c.j, c.k), 1, p.nx + 1,
+  interp8(p, FG, p.has_gp != 0, node_id(p, c.i, c.j, c.k), 1, p.nx + 1,
           (long long)(p.nx + 1) * (p.ny + 1), c.xi, I);
   out[q] = I.es;
   for (int a = 0; a < 3; ++a) {
