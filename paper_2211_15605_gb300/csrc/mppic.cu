@@ -35,6 +35,7 @@ struct mppic_handle {
   double* obj_part = nullptr;  // 3 x nbricks
   double* obj_tmp = nullptr;   // 2 doubles (objectives when the caller passes none)
   int* errs = nullptr;
+  int* zr = nullptr;           // node-layer ranges of deposits (see k_finalize)
   // parcel-sized scratch
   long long cap = 0;
   uint32_t* keys[2] = {nullptr, nullptr};
@@ -171,6 +172,7 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   }
   p.acc = h->acc;
   p.errs = h->errs;
+  p.zr = h->zr;
   p.cstart = h->cstart;
   return p;
 }
@@ -275,6 +277,20 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
   return MPPIC_OK;
 }
 
+// Node pass over the layers deposited into (all layers if full), then roll the ranges.
+template <class T>
+mppic_status launch_finalize(mppic_handle* h, const KParams<T>& p, double* vs_out, bool full) {
+  Phase ph(h, PH_FINALIZE);
+  ph.launched(2);
+  unsigned g = blocks(h->nnode, 256);
+  if (g > 152u * 8u) g = 152u * 8u;
+  k_finalize<T><<<g, 256, 0, h->stream>>>(p, vs_out, full ? 1 : 0);
+  LAUNCHED();
+  k_range_roll<<<1, 1, 0, h->stream>>>(h->zr);
+  LAUNCHED();
+  return MPPIC_OK;
+}
+
 // The Vs accumulator may still hold the deposit a previous push made for positions the
 // caller has since replaced or advanced; a deposit of the current positions starts from zero.
 mppic_status clear_volume_accumulator(mppic_handle* h) {
@@ -311,7 +327,7 @@ mppic_status launch_brick(mppic_handle* h, int mode, const KParams<T>& p, PArray
 // scratch copy if the caller's arrays carry no valid order) and form the node fields.
 template <class T>
 mppic_status deposit_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_gas* gas,
-                          double* vs_out) {
+                          double* vs_out, bool full) {
   PArrays<T> cur = caller_arrays<T>(pc);
   PArrays<T> src = cur;
   if (!h->order_on_caller || h->order_np != pc->np) {
@@ -325,12 +341,8 @@ mppic_status deposit_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_
   if (s) return s;
   s = launch_brick<T>(h, 0, p, src, src, nullptr, pc->np);
   if (s) return s;
-  {
-    Phase ph(h, PH_FINALIZE);
-    ph.launched();
-    k_finalize<T><<<blocks(h->nnode, 256), 256, 0, h->stream>>>(p, vs_out);
-    LAUNCHED();
-  }
+  s = launch_finalize<T>(h, p, vs_out, full);
+  if (s) return s;
   if (gas) h->gas = *gas; else memset(&h->gas, 0, sizeof(h->gas));
   return MPPIC_OK;
 }
@@ -360,12 +372,8 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
       if (s) return s;
       src = sorted_arrays<T>(h, pc->pid != nullptr);
     }
-    {
-      Phase ph(h, PH_FINALIZE);
-      ph.launched();
-      k_finalize<T><<<blocks(h->nnode, 256), 256, 0, h->stream>>>(p, nullptr);
-      LAUNCHED();
-    }
+    s = launch_finalize<T>(h, p, nullptr, false);
+    if (s) return s;
     s = launch_brick<T>(h, 1, p, src, dst, it == nsteps - 1 ? pc->cell : nullptr, np);
     if (s) return s;
     src = dst;
@@ -415,7 +423,7 @@ mppic_status bin_impl(mppic_handle* h, mppic_parcels* pc, int do_sort) {
 
 template <class T>
 mppic_status interp_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_gas* gas, void* out) {
-  mppic_status s = deposit_impl<T>(h, pc, gas, nullptr);
+  mppic_status s = deposit_impl<T>(h, pc, gas, nullptr, false);
   if (s) return s;
   if (pc->np > 0) {
     KParams<T> p = make_params<T>(h, gas);
@@ -495,10 +503,15 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
       alloc(&h->fld, h->tsize * 5 * nnode) && alloc((void**)&h->cstart, sizeof(int) * (nkeys + 1)) &&
       alloc((void**)&h->obj_part, sizeof(double) * 3 * h->nbricks) &&
       alloc((void**)&h->obj_tmp, sizeof(double) * 2) && alloc((void**)&h->errs, sizeof(int)) &&
+      alloc((void**)&h->zr, sizeof(int) * 4) &&
       alloc((void**)&h->totals, sizeof(uint32_t) * 256)) {
     cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(u64) * NQ * h->words * nnode, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->errs, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fld, 0, h->tsize * 5 * nnode, h->stream);
+    // no deposit yet; the first finalize covers every layer
+    const int zr0[4] = {1 << 30, -1, 0, cfg->nz};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->zr, zr0, sizeof(zr0), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = fail(h, MPPIC_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   }
   if (s) {
@@ -523,8 +536,9 @@ mppic_status mppic_deposit(mppic_handle* h, const mppic_parcels* parcels, const 
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
   mppic_status s = check_parcels(h, parcels);
   if (s) return s;
-  s = h->cfg.precision == 32 ? deposit_impl<float>(h, parcels, gas, Vs_out)
-                             : deposit_impl<double>(h, parcels, gas, Vs_out);
+  const bool full = Vs_out != nullptr || fields_out != nullptr;
+  s = h->cfg.precision == 32 ? deposit_impl<float>(h, parcels, gas, Vs_out, full)
+                             : deposit_impl<double>(h, parcels, gas, Vs_out, full);
   if (s) return s;
   if (fields_out)
     CU(cudaMemcpyAsync(fields_out, h->fld, h->tsize * 5 * h->nnode, cudaMemcpyDeviceToDevice,
@@ -613,7 +627,7 @@ long long mppic_num_nodes(const mppic_handle* h) { return h ? h->nnode : 0; }
 void mppic_destroy(mppic_handle* h) {
   if (!h) return;
   cudaFree(h->acc); cudaFree(h->fld); cudaFree(h->cstart); cudaFree(h->obj_part);
-  cudaFree(h->obj_tmp); cudaFree(h->errs); cudaFree(h->totals); cudaFree(h->hist);
+  cudaFree(h->obj_tmp); cudaFree(h->errs); cudaFree(h->zr); cudaFree(h->totals); cudaFree(h->hist);
   for (int i = 0; i < 2; ++i) { cudaFree(h->keys[i]); cudaFree(h->vals[i]); }
   for (int f = 0; f < 8; ++f) cudaFree(h->sorted[f]);
   cudaFree(h->sorted_pid);

@@ -62,6 +62,7 @@ struct KParams {
   const T* U[3];
   u64* acc;                  // [NQ][words][nnode]
   int* errs;
+  int* zr;                   // node-layer ranges: [0,1] touched by the last deposit, [2,3] last finalized
   const int* cstart;         // [nkeys+1]: first sorted parcel of each brick-major key
 };
 
@@ -772,6 +773,7 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
   for (int a = 0; a < 3; ++a) FG.g[a] = p.gpf[a];
   const long long sxg = 1, syg = p.nx + 1, szg = (long long)(p.nx + 1) * (p.ny + 1);
   T o_dp = 0, o_hn = 0, o_vs = 0;
+  int kdep_lo = 1 << 30, kdep_hi = -1;          // node layers this CTA deposits into
   const int nchunks = (pend - pstart + NC - 1) / NC;
   if (tid == 0) issue_chunk(src, pstart, min(NC, pend - pstart), np, stage, &mbar[0]);
 
@@ -817,6 +819,8 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
       const int ti = c.i - bi0, tj = c.j - bj0, tk = c.k - bk0;
       const bool inb = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
       rkey[r] = inb ? ti + BX * (tj + BY * tk) : BCELLS;
+      kdep_lo = min(kdep_lo, c.k);
+      kdep_hi = max(kdep_hi, c.k + 1);
       if (MODE == 0) {
         rxn[r] = c.xi[0]; rxn[NC + r] = c.xi[1]; rxn[2 * NC + r] = c.xi[2];
         rcn[r] = oldcell;
@@ -860,6 +864,8 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
       Cell3<T> cnw;
       bin3(p, pos[0], pos[1], pos[2], cnw);
       const int newcell = cell_id(p, cnw.i, cnw.j, cnw.k);
+      kdep_lo = min(kdep_lo, cnw.k);
+      kdep_hi = max(kdep_hi, cnw.k + 1);
       rxn[r] = cnw.xi[0]; rxn[NC + r] = cnw.xi[1]; rxn[2 * NC + r] = cnw.xi[2];
       rcn[r] = newcell;
       dst.a[0][q] = pos[0]; dst.a[1][q] = pos[1]; dst.a[2][q] = pos[2];
@@ -1022,6 +1028,10 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
     }
     __syncthreads();
   }
+  // ---- node layers touched by this CTA's deposits, for the next finalize
+  kdep_lo = __reduce_min_sync(0xffffffffu, kdep_lo);
+  kdep_hi = __reduce_max_sync(0xffffffffu, kdep_hi);
+  if (lane == 0 && kdep_hi >= 0) { atomicMin(&p.zr[0], kdep_lo); atomicMax(&p.zr[1], kdep_hi); }
   // ---- the tile, in exact fixed point, to the global accumulators
   const int nq = MODE == 1 ? NQ : 1;
   for (int e = tid; e < nq * TNODES; e += BCELLS) {
@@ -1044,14 +1054,36 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
 // a5: node fields from the deposited volume. Reads and clears the Vs accumulator and
 // clears the drag-sum accumulators for the coming push. vs_out (nullable) receives Vs.
 template <class T>
-__global__ void k_finalize(KParams<T> p, double* __restrict__ vs_out) {
+__device__ __forceinline__ void finalize_node(const KParams<T>& p, int n, int i, int j, int k,
+                                              double* vs_out);
+
+template <class T>
+__global__ void k_finalize(KParams<T> p, double* __restrict__ vs_out, int full) {
   constexpr int W = Words<T>::n;
-  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.nnode) return;
-  int i = (int)(n % (p.nx + 1));
-  long long r = n / (p.nx + 1);
-  int j = (int)(r % (p.ny + 1));
-  int k = (int)(r / (p.ny + 1));
+  const int nx1 = p.nx + 1, ny1 = p.ny + 1;
+  const int layer = nx1 * ny1;
+  int klo = 0, khi = p.nz;
+  if (!full) {               // layers deposited into now or at the previous finalize
+    klo = max(0, min(p.zr[0], p.zr[2]));
+    khi = min(p.nz, max(p.zr[1], p.zr[3]));
+  }
+  const int n0 = klo * layer, n1 = (khi + 1) * layer;
+  for (int n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += gridDim.x * blockDim.x)
+    finalize_node(p, n, n % nx1, (n / nx1) % ny1, n / layer, vs_out);
+}
+
+// Moves the deposit's layer range to "last finalized" and empties it for the next deposit.
+__global__ void k_range_roll(int* zr) {
+  zr[2] = zr[0];
+  zr[3] = zr[1];
+  zr[0] = 1 << 30;
+  zr[1] = -1;
+}
+
+template <class T>
+__device__ __forceinline__ void finalize_node(const KParams<T>& p, int n, int i, int j, int k,
+                                              double* vs_out) {
+  constexpr int W = Words<T>::n;
   u64 fx[W];
   for (int w = 0; w < W; ++w) { fx[w] = p.acc[(long long)w * p.nnode + n]; }
   if (W == 1 && (long long)fx[0] >= (1ll << 62)) atomicOr(p.errs, ERR_RANGE);
