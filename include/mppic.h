@@ -130,6 +130,26 @@ mppic_status mppic_interp(mppic_handle *h, const mppic_parcels *parcels, const m
 mppic_status mppic_step(mppic_handle *h, mppic_parcels *parcels, const mppic_gas *gas,
                         int nsteps, double *obj_out);
 
+/* Change the three differentiable parameters (drag multiplier C, diameter scale s_d, inflow
+ * velocity u_in) of the handle's config for subsequent calls. dscale must be positive. */
+mppic_status mppic_set_params(mppic_handle *h, double drag_mult, double dscale, double u_in);
+
+/* Reverse mode, part 1. With every > 0, each following mppic_step call saves the parcel
+ * state (in handle memory, 8 arrays and an identity tag per saved state) at its first step
+ * and every `every` steps after, so that mppic_backward can differentiate that call.
+ * every = 0 switches checkpointing off. */
+mppic_status mppic_checkpoint(mppic_handle *h, int every);
+
+/* Reverse mode, part 2: the gradient of L = a <dP> + b <H> over the steps of the last
+ * checkpointed mppic_step call, where <.> is the average over its steps of the objectives
+ * that call returned, with respect to (drag multiplier C, diameter scale s_d, inflow
+ * velocity u_in). dL_d_dP_H (host, 2 doubles) = (a, b); grad_out (host, 3 doubles) receives
+ * (dL/dC, dL/ds_d, dL/du_in). Hand-written adjoints of the push, drag, walls, objectives,
+ * interpolation (its transpose is a deposit) and deposit (its transpose is a gather); the
+ * states between checkpoints are recomputed without sorting. Synchronous. Afterwards the
+ * handle's node fields belong to a recomputed state; the next call recomputes them. */
+mppic_status mppic_backward(mppic_handle *h, const double *dL_d_dP_H, double *grad_out);
+
 /* The drag sums of the last step of the last mppic_step call, as doubles (device arrays of
  * nnode values; any may be NULL): A and B[3]. */
 mppic_status mppic_drag_sums(mppic_handle *h, double *A, double *Bx, double *By, double *Bz);

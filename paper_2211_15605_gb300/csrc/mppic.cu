@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/mppic.h"
+#include "mppic_adjoint.cuh"
 #include "mppic_device.cuh"
 
 using namespace mppic;
@@ -51,6 +52,25 @@ struct mppic_handle {
   long long step_counter = 0;
   // last gas seen by deposit (node grad p arrays are read by later pushes)
   mppic_gas gas{};
+  // reverse mode: identity tags carried through sorts and the saved segment states
+  int ckpt_every = 0;
+  int* tag = nullptr;          // identity of the parcel at each caller position
+  int* sorted_tag = nullptr;   // the same for the sorted copy
+  long long tag_cap = 0;
+  std::vector<void*> ckpt;     // per checkpoint: 8 parcel arrays then the tags
+  long long ckpt_np = 0;
+  int last_nsteps = -1;
+  // backward buffers
+  double* adj = nullptr;       // 6 x np: adjoint of x, y, z, u, v, w
+  double* adj_tmp = nullptr;   // 6 x np
+  double* Vb = nullptr;        // np
+  double* nadj = nullptr;      // 6 x nnode
+  int* inv = nullptr;          // np
+  void* work = nullptr;        // 8 x np parcel arrays of the segment being recomputed
+  void* seg = nullptr;         // ckpt_every x 6 x np saved states
+  double* theta = nullptr;     // 3 gradient accumulators + 2 height sums
+  long long adj_np = 0;
+  int seg_len = 0;
   // profiling: event pairs recorded around each phase while enabled
   bool prof = false;
   std::vector<cudaEvent_t> ev;         // start/stop pairs
@@ -154,6 +174,8 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   p.kRe = (T)(c.rho_g / c.mu_g);
   p.kD1 = (T)(c.drag_mult * 18.0 * c.mu_g / c.rho_p);
   p.kD2 = (T)(c.drag_mult * 0.33 * c.rho_g / c.rho_p);
+  p.kD1u = (T)(18.0 * c.mu_g / c.rho_p);
+  p.kD2u = (T)(0.33 * c.rho_g / c.rho_p);
   // Fixed-point units: Vs in cell volumes, A and B in rho_p * cell volume per second.
   const int SV = sizeof(T) == 4 ? 48 : 96, SA = sizeof(T) == 4 ? 40 : 88;
   double mV = std::ldexp(1.0, SV) / p.vcell;
@@ -178,19 +200,21 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
 }
 
 template <class T>
-PArrays<T> caller_arrays(const mppic_parcels* pc) {
+PArrays<T> caller_arrays(const mppic_parcels* pc, int* tag = nullptr) {
   PArrays<T> a;
   void* const src[8] = {pc->x, pc->y, pc->z, pc->u, pc->v, pc->w, pc->d, pc->omega};
   for (int f = 0; f < 8; ++f) a.a[f] = static_cast<T*>(src[f]);
   a.pid = pc->pid;
+  a.tag = tag;
   return a;
 }
 
 template <class T>
-PArrays<T> sorted_arrays(mppic_handle* h, bool with_pid) {
+PArrays<T> sorted_arrays(mppic_handle* h, bool with_pid, bool with_tag = false) {
   PArrays<T> a;
   for (int f = 0; f < 8; ++f) a.a[f] = static_cast<T*>(h->sorted[f]);
   a.pid = with_pid ? h->sorted_pid : nullptr;
+  a.tag = with_tag ? h->sorted_tag : nullptr;
   return a;
 }
 
@@ -262,8 +286,8 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
       ph.launched(3);
       src = 1 - src;
     }
-    k_gather<T><<<blocks(np, 256), 256, 0, st>>>(cur, sorted_arrays<T>(h, cur.pid != nullptr),
-                                                  h->vals[src], np);
+    k_gather<T><<<blocks(np, 256), 256, 0, st>>>(
+        cur, sorted_arrays<T>(h, cur.pid != nullptr, cur.tag != nullptr), h->vals[src], np);
     LAUNCHED();
     k_cell_starts<<<blocks(h->nkeys + 1, 256), 256, 0, st>>>(h->keys[src], np, h->nkeys,
                                                              h->cstart);
@@ -347,18 +371,64 @@ mppic_status deposit_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_
   return MPPIC_OK;
 }
 
+// Identity tags and checkpoint storage for a step call with checkpointing.
+mppic_status prepare_checkpoints(mppic_handle* h, long long np, int nsteps) {
+  if (np > h->tag_cap) {
+    cudaFree(h->tag); cudaFree(h->sorted_tag);
+    h->tag = h->sorted_tag = nullptr;
+    h->tag_cap = 0;
+    CU(cudaMalloc(&h->tag, sizeof(int) * (np > 0 ? np : 1)));
+    CU(cudaMalloc(&h->sorted_tag, sizeof(int) * (np > 0 ? np : 1)));
+    h->tag_cap = np;
+  }
+  const int K = h->ckpt_every;
+  const size_t need = (size_t)((nsteps + K - 1) / K > 0 ? (nsteps + K - 1) / K : 1);
+  if (np != h->ckpt_np) {
+    for (void* c : h->ckpt) cudaFree(c);
+    h->ckpt.clear();
+    h->ckpt_np = np;
+  }
+  while (h->ckpt.size() < need) {
+    void* c = nullptr;
+    CU(cudaMalloc(&c, (8 * h->tsize + sizeof(int)) * (size_t)(np > 0 ? np : 1)));
+    h->ckpt.push_back(c);
+  }
+  if (np > 0) {
+    k_iota<<<blocks(np, 256), 256, 0, h->stream>>>(h->tag, np);
+    LAUNCHED();
+  }
+  return MPPIC_OK;
+}
+
+template <class T>
+mppic_status save_checkpoint(mppic_handle* h, int idx, const PArrays<T>& src, long long np) {
+  if (np == 0) return MPPIC_OK;
+  char* c = static_cast<char*>(h->ckpt[idx]);
+  for (int f = 0; f < 8; ++f)
+    CU(cudaMemcpyAsync(c + (size_t)f * np * h->tsize, src.a[f], np * h->tsize,
+                       cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(c + (size_t)8 * np * h->tsize, src.tag, np * sizeof(int),
+                     cudaMemcpyDeviceToDevice, h->stream));
+  return MPPIC_OK;
+}
+
 template <class T>
 mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas, int nsteps,
                        double* obj_out) {
   const long long np = pc->np;
-  PArrays<T> dst = caller_arrays<T>(pc);
+  const bool ck = h->ckpt_every > 0;
+  if (ck) {
+    mppic_status s = prepare_checkpoints(h, np, nsteps);
+    if (s) return s;
+  }
+  PArrays<T> dst = caller_arrays<T>(pc, ck ? h->tag : nullptr);
   PArrays<T> src = dst;
   const int every = h->cfg.sort_every;
   auto sort_due = [&](long long step) { return every > 0 && step % every == 0; };
   if (!h->order_on_caller || h->order_np != np || sort_due(h->step_counter)) {
     mppic_status s = sort_into_scratch<T>(h, pc, dst);
     if (s) return s;
-    src = sorted_arrays<T>(h, pc->pid != nullptr);
+    src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
   }
   KParams<T> p = make_params<T>(h, gas);
   mppic_status s = clear_volume_accumulator(h);
@@ -370,7 +440,11 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
     if (it > 0 && sort_due(h->step_counter + it)) {
       s = sort_into_scratch<T>(h, pc, dst);
       if (s) return s;
-      src = sorted_arrays<T>(h, pc->pid != nullptr);
+      src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
+    }
+    if (ck && it % h->ckpt_every == 0) {
+      s = save_checkpoint<T>(h, it / h->ckpt_every, src, np);
+      if (s) return s;
     }
     s = launch_finalize<T>(h, p, nullptr, false);
     if (s) return s;
@@ -392,7 +466,113 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   h->order_on_caller = true;
   h->order_np = np;
   h->step_counter += nsteps;
+  h->last_nsteps = ck ? nsteps : -1;
   if (gas) h->gas = *gas; else memset(&h->gas, 0, sizeof(h->gas));
+  return MPPIC_OK;
+}
+
+// Reverse sweep over the last checkpointed mppic_step call (see mppic_backward).
+template <class T>
+mppic_status backward_impl(mppic_handle* h, const double* dL, double* grad_out) {
+  const long long np = h->ckpt_np;
+  const int N = h->last_nsteps, K = h->ckpt_every;
+  const size_t ts = h->tsize;
+  if (np > h->adj_np || h->seg_len < K) {
+    cudaFree(h->adj); cudaFree(h->adj_tmp); cudaFree(h->Vb); cudaFree(h->inv);
+    cudaFree(h->work); cudaFree(h->seg);
+    h->adj = h->adj_tmp = h->Vb = nullptr; h->inv = nullptr; h->work = h->seg = nullptr;
+    h->adj_np = 0; h->seg_len = 0;
+    const size_t n1 = (size_t)(np > 0 ? np : 1);
+    CU(cudaMalloc(&h->adj, sizeof(double) * 6 * n1));
+    CU(cudaMalloc(&h->adj_tmp, sizeof(double) * 6 * n1));
+    CU(cudaMalloc(&h->Vb, sizeof(double) * n1));
+    CU(cudaMalloc(&h->inv, sizeof(int) * n1));
+    CU(cudaMalloc(&h->work, ts * 8 * n1));
+    CU(cudaMalloc(&h->seg, ts * 6 * n1 * (size_t)K));
+    h->adj_np = np; h->seg_len = K;
+  }
+  if (!h->nadj) CU(cudaMalloc(&h->nadj, sizeof(double) * 6 * h->nnode));
+  if (!h->theta) CU(cudaMalloc(&h->theta, sizeof(double) * 5));
+  cudaStream_t st = h->stream;
+  CU(cudaMemsetAsync(h->theta, 0, sizeof(double) * 5, st));
+  CU(cudaMemsetAsync(h->adj, 0, sizeof(double) * 6 * (np > 0 ? np : 1), st));
+  KParams<T> p = make_params<T>(h, &h->gas);
+  const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
+  AdjWeights aw;
+  aw.a_dp = dL[0] / N / area;
+  aw.a_h = dL[1] / N;
+  T* work = static_cast<T*>(h->work);
+  T* wa[8];
+  for (int f = 0; f < 8; ++f) wa[f] = work + (size_t)f * np;
+  const unsigned gp = blocks(np > 0 ? np : 1, 256);
+  const int nseg = (N + K - 1) / K;
+  // deposit of the state in `st6` (6 arrays) with d, omega of the work arrays, then node fields
+  auto node_fields = [&](T* const* xs) -> mppic_status {
+    CU(cudaMemsetAsync(h->acc, 0, sizeof(u64) * h->words * h->nnode, st));
+    if (np > 0) {
+      k_dep_simple<T><<<gp, 256, 0, st>>>(p, xs[0], xs[1], xs[2], wa[6], wa[7], np);
+      LAUNCHED();
+    }
+    return launch_finalize<T>(h, p, nullptr, true);
+  };
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int s0 = sg * K, len = (N - s0) < K ? (N - s0) : K;
+    const char* c = static_cast<const char*>(h->ckpt[sg]);
+    if (np > 0) CU(cudaMemcpyAsync(work, c, ts * 8 * np, cudaMemcpyDeviceToDevice, st));
+    if (sg < nseg - 1 && np > 0) {   // adjoint state from the next segment's parcel order
+      const int* tag_next = reinterpret_cast<const int*>(static_cast<const char*>(h->ckpt[sg + 1]) + ts * 8 * np);
+      const int* tag_this = reinterpret_cast<const int*>(c + ts * 8 * np);
+      k_tag_inverse<<<gp, 256, 0, st>>>(tag_next, np, h->inv);
+      k_adj_reorder<<<gp, 256, 0, st>>>(h->adj, h->adj_tmp, tag_this, h->inv, np);
+      LAUNCHED();
+      std::swap(h->adj, h->adj_tmp);
+    }
+    // recompute the segment's states S_s0 .. S_s0+len-1
+    T* seg = static_cast<T*>(h->seg);
+    for (int t = 0; t < len; ++t) {
+      if (np > 0)
+        CU(cudaMemcpyAsync(seg + (size_t)t * 6 * np, work, ts * 6 * np, cudaMemcpyDeviceToDevice, st));
+      if (t < len - 1) {
+        mppic_status s = node_fields(wa);
+        if (s) return s;
+        if (np > 0) {
+          k_push_simple<T><<<gp, 256, 0, st>>>(p, wa[0], wa[1], wa[2], wa[3], wa[4], wa[5], wa[6],
+                                               wa[7], np);
+          LAUNCHED();
+        }
+      }
+    }
+    // reverse sweep through the segment
+    for (int t = len - 1; t >= 0; --t) {
+      T* xs[6];
+      for (int f = 0; f < 6; ++f) xs[f] = seg + ((size_t)t * 6 + f) * np;
+      mppic_status s = node_fields(xs);
+      if (s) return s;
+      CU(cudaMemsetAsync(h->theta + 3, 0, sizeof(double) * 2, st));
+      CU(cudaMemsetAsync(h->nadj, 0, sizeof(double) * 6 * h->nnode, st));
+      if (np > 0) {
+        k_height_sums<T><<<gp, 256, 0, st>>>(p, xs[2], wa[6], wa[7], np, h->theta + 3);
+        k_adj_parcel<T><<<gp, 256, 0, st>>>(p, xs[0], xs[1], xs[2], xs[3], xs[4], xs[5], wa[6], wa[7],
+                                             np, h->adj, h->adj + 3 * np, h->Vb, h->nadj,
+                                             h->theta + 3, aw, h->theta);
+        LAUNCHED();
+      }
+      k_adj_node<T><<<blocks(h->nnode, 256), 256, 0, st>>>(p, h->nadj, h->theta);
+      LAUNCHED();
+      if (np > 0) {
+        k_adj_deposit<T><<<gp, 256, 0, st>>>(p, xs[0], xs[1], xs[2], wa[6], wa[7], np, h->adj,
+                                              h->Vb, h->nadj, h->theta);
+        LAUNCHED();
+      }
+    }
+  }
+  double th[3];
+  CU(cudaMemcpyAsync(th, h->theta, sizeof(th), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  for (int i = 0; i < 3; ++i) grad_out[i] = th[i];
+  // the node arrays now hold a recomputed state: the next call re-deposits and finalizes all
+  const int zr0[4] = {1 << 30, -1, 0, h->cfg.nz};
+  CU(cudaMemcpy(h->zr, zr0, sizeof(zr0), cudaMemcpyHostToDevice));
   return MPPIC_OK;
 }
 
@@ -566,6 +746,33 @@ mppic_status mppic_step(mppic_handle* h, mppic_parcels* parcels, const mppic_gas
                                 : step_impl<double>(h, parcels, gas, nsteps, obj_out);
 }
 
+mppic_status mppic_set_params(mppic_handle* h, double drag_mult, double dscale, double u_in) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (!(dscale > 0)) return fail(h, MPPIC_ERR_INVALID, "dscale must be positive");
+  h->cfg.drag_mult = drag_mult;
+  h->cfg.dscale = dscale;
+  h->cfg.u_in = u_in;
+  return MPPIC_OK;
+}
+
+mppic_status mppic_checkpoint(mppic_handle* h, int every) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (every < 0) return fail(h, MPPIC_ERR_INVALID, "every must be >= 0");
+  h->ckpt_every = every;
+  h->last_nsteps = -1;
+  return MPPIC_OK;
+}
+
+mppic_status mppic_backward(mppic_handle* h, const double* dL_d_dP_H, double* grad_out) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (!dL_d_dP_H || !grad_out) return fail(h, MPPIC_ERR_INVALID, "dL and grad_out must not be NULL");
+  if (h->ckpt_every <= 0 || h->last_nsteps <= 0)
+    return fail(h, MPPIC_ERR_INVALID,
+                "no checkpointed mppic_step call to differentiate (call mppic_checkpoint first)");
+  return h->cfg.precision == 32 ? backward_impl<float>(h, dL_d_dP_H, grad_out)
+                                : backward_impl<double>(h, dL_d_dP_H, grad_out);
+}
+
 mppic_status mppic_drag_sums(mppic_handle* h, double* A, double* Bx, double* By, double* Bz) {
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
   return h->cfg.precision == 32 ? drag_impl<float>(h, A, Bx, By, Bz)
@@ -632,6 +839,10 @@ void mppic_destroy(mppic_handle* h) {
   for (int f = 0; f < 8; ++f) cudaFree(h->sorted[f]);
   cudaFree(h->sorted_pid);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  cudaFree(h->tag); cudaFree(h->sorted_tag);
+  for (void* c : h->ckpt) cudaFree(c);
+  cudaFree(h->adj); cudaFree(h->adj_tmp); cudaFree(h->Vb); cudaFree(h->nadj); cudaFree(h->inv);
+  cudaFree(h->work); cudaFree(h->seg); cudaFree(h->theta);
   delete h;
 }
 

@@ -52,6 +52,7 @@ struct KParams {
   T inv_rho_p;               // 1 / rho_p
   T kRe;                     // rho_g / mu_g (Re_m = eps_g d |s| kRe)
   T kD1, kD2;                // C 18 mu / rho_p and C 0.33 rho_g / rho_p (drag prefactors)
+  T kD1u, kD2u;              // the same without C
   T mV, mA;                  // fixed-point multipliers (value * m = integer units)
   double inv_mV, inv_mA;
   T u_in;
@@ -453,7 +454,8 @@ __global__ void k_cell_starts(const uint32_t* __restrict__ skey, long long n, lo
 template <class T>
 struct PArrays {
   T* a[8];        // x y z u v w d omega
-  int* pid;
+  int* pid;       // caller's identity array (optional)
+  int* tag;       // the handle's identity array while checkpointing (optional)
 };
 
 template <class T>
@@ -465,6 +467,7 @@ __global__ void k_gather(PArrays<T> src, PArrays<T> dst, const uint32_t* __restr
 #pragma unroll
   for (int f = 0; f < 8; ++f) dst.a[f][q] = src.a[f][s];
   if (src.pid) dst.pid[q] = src.pid[s];
+  if (src.tag) dst.tag[q] = src.tag[s];
 }
 
 // ------------------------------------------------------------ brick CTA --
@@ -873,6 +876,7 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
       if (src.a[0] != dst.a[0]) {
         dst.a[6][q] = d; dst.a[7][q] = om;
         if (src.pid) dst.pid[q] = src.pid[q];
+        if (src.tag) dst.tag[q] = src.tag[q];
       }
       if (cell_out) cell_out[q] = newcell;
     }
@@ -1059,7 +1063,6 @@ __device__ __forceinline__ void finalize_node(const KParams<T>& p, int n, int i,
 
 template <class T>
 __global__ void k_finalize(KParams<T> p, double* __restrict__ vs_out, int full) {
-  constexpr int W = Words<T>::n;
   const int nx1 = p.nx + 1, ny1 = p.ny + 1;
   const int layer = nx1 * ny1;
   int klo = 0, khi = p.nz;

@@ -95,6 +95,12 @@ def load():
         L.mppic_drag_sums.restype = st
         L.mppic_check.argtypes = [H]
         L.mppic_check.restype = st
+        L.mppic_set_params.argtypes = [H, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.mppic_set_params.restype = st
+        L.mppic_checkpoint.argtypes = [H, ctypes.c_int]
+        L.mppic_checkpoint.restype = st
+        L.mppic_backward.argtypes = [H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.mppic_backward.restype = st
         L.mppic_profile_enable.argtypes = [H, ctypes.c_int]
         L.mppic_profile_enable.restype = st
         L.mppic_profile_read.argtypes = [H, ctypes.POINTER(Profile)]
@@ -242,6 +248,22 @@ class Bed:
         self._ok(self.L.mppic_drag_sums(self.h, _ptr(A), _ptr(B[0]), _ptr(B[1]), _ptr(B[2])))
         return A, B
 
+    def set_params(self, drag_mult: float, dscale: float, u_in: float):
+        """Set the three differentiable parameters (C, s_d, u_in) for later calls."""
+        self._ok(self.L.mppic_set_params(self.h, float(drag_mult), float(dscale), float(u_in)))
+
+    def checkpoint(self, every: int):
+        """Save the parcel state every `every` steps in later step calls (0 = off)."""
+        self._ok(self.L.mppic_checkpoint(self.h, int(every)))
+
+    def backward(self, dL_ddP: float, dL_dH: float):
+        """Gradient of dL_ddP <dP> + dL_dH <H> over the last checkpointed step call with
+        respect to (C, s_d, u_in), as a tuple of three floats."""
+        dl = (ctypes.c_double * 2)(float(dL_ddP), float(dL_dH))
+        g = (ctypes.c_double * 3)()
+        self._ok(self.L.mppic_backward(self.h, dl, g))
+        return (g[0], g[1], g[2])
+
     def profile(self, enable: bool = True):
         """Enable or disable per-phase CUDA-event timing inside the library (resets counters)."""
         self._ok(self.L.mppic_profile_enable(self.h, int(enable)))
@@ -267,3 +289,29 @@ class Bed:
             self.close()
         except Exception:
             pass
+
+
+class BedObjectives(torch.autograd.Function):
+    """Time-averaged (dP, H) of nsteps coupling steps as a differentiable function of
+    theta = (drag multiplier C, diameter scale s_d, inflow velocity u_in).
+
+    forward runs mppic_step with checkpointing on a copy of the parcel state; backward
+    calls mppic_backward (hand-written adjoint kernels). theta is a CPU or CUDA tensor of
+    3 values; the result is a float64 tensor (<dP>, <H>) on the parcels' device.
+    """
+
+    @staticmethod
+    def forward(ctx, theta, bed: "Bed", parcels: dict, gas, nsteps: int, every: int = 20):
+        th = [float(t) for t in theta.detach().cpu().tolist()]
+        bed.set_params(*th)
+        bed.checkpoint(every)
+        state = {k: v.clone() for k, v in parcels.items()}
+        obj = bed.step(state, gas, nsteps)
+        ctx.bed = bed
+        return obj.mean(0)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = grad_out.detach().double().cpu().tolist()
+        grad = ctx.bed.backward(g[0], g[1])
+        return torch.tensor(grad, dtype=torch.float64), None, None, None, None, None
