@@ -93,10 +93,22 @@ typedef struct {
   const void *gradp[3];
 } mppic_gas;
 
-/* Create a handle for one bed (nbeds must be 1; bed_parcel_offsets and per_bed must be
- * NULL). stream is a cudaStream_t (NULL = legacy default stream). The handle binds to
- * the current CUDA device. Returns MPPIC_ERR_INVALID for sizes whose cell or node count
- * overflows int32, non-positive spacing or dt, or an unknown precision. */
+/* Create a handle for one bed (nbeds = 1; bed_parcel_offsets and per_bed may be NULL) or
+ * for a batch of nbeds independent beds advanced together. For a batch:
+ *   - per_bed (host, nbeds configs) gives each bed's grid and physics; precision and
+ *     sort_every come from cfg;
+ *   - bed_parcel_offsets (host, nbeds+1, starting at 0) gives each bed's parcel range in
+ *     the one concatenated set of parcel arrays passed to mppic_bin / mppic_step;
+ *   - node arrays (gas U / grad p) are concatenated in bed order, each bed's
+ *     (nx+1)(ny+1)(nz+1) nodes after the previous bed's;
+ *   - mppic_step's obj_out is [nsteps][nbeds][2];
+ *   - mppic_deposit, mppic_interp, mppic_drag_sums and reverse mode take single-bed
+ *     handles only.
+ * All beds share one sort (keys are global brick, local cell; each bed's parcels keep their
+ * range) and one persistent launch of each kernel per step. stream is a cudaStream_t
+ * (NULL = legacy default stream). The handle binds to the current CUDA device. Returns
+ * MPPIC_ERR_INVALID for sizes whose cell, node or key count overflows int32, non-positive
+ * spacing, dt or dscale, or an unknown precision. */
 mppic_status mppic_create(const mppic_config *cfg, int nbeds, const long long *bed_parcel_offsets,
                           const mppic_config *per_bed, void *stream, mppic_handle **out);
 
@@ -200,7 +212,11 @@ mppic_status mppic_profile_read(mppic_handle *h, mppic_profile *out);
 mppic_status mppic_deposit_static(const mppic_config *cfg, const mppic_parcels *parcels,
                                   double *Vs_out, void *stream);
 
-/* Node count (nx+1)(ny+1)(nz+1) of the handle's bed. */
+/* Launch tuning: the persistent step and deposit kernels use grid_per_sm CTAs per SM
+ * (0 = as many as fit at once, the default). Results do not depend on it. */
+mppic_status mppic_tune(mppic_handle *h, int grid_per_sm);
+
+/* Node count (nx+1)(ny+1)(nz+1) of the handle's bed (all beds of a batch). */
 long long mppic_num_nodes(const mppic_handle *h);
 
 void mppic_destroy(mppic_handle *h);

@@ -22,6 +22,20 @@ using namespace mppic;
 
 struct mppic_handle {
   mppic_config cfg;
+  // batch of independent beds (nbeds == 1: a single bed, described by cfg)
+  int nbeds = 1;
+  std::vector<mppic_config> bed_cfg;
+  std::vector<long long> poff, noff, boff;       // first parcel / node / brick of each bed
+  long long* d_poff = nullptr;
+  long long* d_noff = nullptr;
+  long long* d_boff = nullptr;
+  int* d_brick_bed = nullptr;
+  double* d_area = nullptr;
+  void* d_beds = nullptr;                        // KParams<T>[nbeds]
+  std::vector<unsigned char> beds_host;          // last uploaded copy
+  unsigned long long* wq = nullptr;              // persistent-kernel work counter
+  int nsm = 0;
+  int grid_factor = 0;                           // persistent CTAs per SM (0: resident maximum)
   cudaStream_t stream = nullptr;
   int device = 0;
   int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0;
@@ -153,6 +167,9 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   p.nbx = h->nbx; p.nby = h->nby; p.nbz = h->nbz;
   p.nnode = h->nnode;
   p.nbricks = h->nbricks;
+  p.nbase = 0;
+  p.bbase = 0;
+  p.nstride = h->nnode;
   const double hs[3] = {c.dx, c.dy, c.dz};
   const int ns[3] = {c.nx, c.ny, c.nz};
   for (int a = 0; a < 3; ++a) {
@@ -197,6 +214,52 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   p.zr = h->zr;
   p.cstart = h->cstart;
   return p;
+}
+
+// Per-bed parameters of a batch, uploaded when they change. Node-field and gas pointers
+// point at each bed's slice of the concatenated node arrays.
+template <class T>
+mppic_status upload_beds(mppic_handle* h, const mppic_gas* gas, const KParams<T>** out) {
+  *out = nullptr;
+  if (h->nbeds == 1) return MPPIC_OK;
+  std::vector<KParams<T>> v(h->nbeds);
+  for (int b = 0; b < h->nbeds; ++b) {
+    mppic_handle tmp;                       // only cfg/geometry/pointers are read by make_params
+    tmp.cfg = h->bed_cfg[b];
+    tmp.cfg.precision = h->cfg.precision;
+    const mppic_config& c = tmp.cfg;
+    tmp.nbx = (c.nx + BX - 1) / BX; tmp.nby = (c.ny + BY - 1) / BY; tmp.nbz = (c.nz + BZ - 1) / BZ;
+    tmp.nnode = h->noff[b + 1] - h->noff[b];
+    tmp.nbricks = h->boff[b + 1] - h->boff[b];
+    tmp.fld = h->fld; tmp.acc = h->acc; tmp.errs = h->errs; tmp.cstart = h->cstart; tmp.zr = h->zr;
+    KParams<T> p = make_params<T>(&tmp, nullptr);
+    p.nbase = h->noff[b];
+    p.bbase = h->boff[b];
+    p.nstride = h->nnode;
+    T* f = static_cast<T*>(h->fld);
+    for (int k = 0; k < 5; ++k) p.fld[k] = f + (long long)k * h->nnode + h->noff[b];
+    p.has_gp = 0;
+    if (gas) {
+      for (int a = 0; a < 3; ++a)
+        p.U[a] = gas->U[a] ? static_cast<const T*>(gas->U[a]) + h->noff[b] : nullptr;
+      if (gas->gradp[0] && gas->gradp[1] && gas->gradp[2]) {
+        p.has_gp = 1;
+        for (int a = 0; a < 3; ++a) p.gpf[a] = static_cast<const T*>(gas->gradp[a]) + h->noff[b];
+      }
+    }
+    tmp.fld = nullptr; tmp.acc = nullptr; tmp.errs = nullptr; tmp.cstart = nullptr; tmp.zr = nullptr;
+    v[b] = p;
+  }
+  const size_t bytes = sizeof(KParams<T>) * h->nbeds;
+  if (!h->d_beds) CU(cudaMalloc(&h->d_beds, bytes));
+  if (h->beds_host.size() != bytes || memcmp(h->beds_host.data(), v.data(), bytes) != 0) {
+    h->beds_host.assign(reinterpret_cast<unsigned char*>(v.data()),
+                        reinterpret_cast<unsigned char*>(v.data()) + bytes);
+    CU(cudaMemcpyAsync(h->d_beds, h->beds_host.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  *out = static_cast<const KParams<T>*>(h->d_beds);
+  return MPPIC_OK;
 }
 
 template <class T>
@@ -266,11 +329,18 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
   mppic_status s = ensure_capacity(h, np, pc->pid != nullptr);
   if (s) return s;
   KParams<T> p = make_params<T>(h, nullptr);
+  const KParams<T>* beds = nullptr;
+  s = upload_beds<T>(h, nullptr, &beds);
+  if (s) return s;
   cudaStream_t st = h->stream;
   Phase ph(h, PH_SORT);
   if (np > 0) {
-    k_keys<T><<<blocks(np, 256), 256, 0, st>>>(p, cur.a[0], cur.a[1], cur.a[2], h->keys[0],
-                                                h->vals[0], np);
+    if (beds)
+      k_keys_b<T><<<blocks(np, 256), 256, 0, st>>>(beds, h->d_poff, h->nbeds, cur.a[0], cur.a[1],
+                                                    cur.a[2], h->keys[0], h->vals[0], np);
+    else
+      k_keys<T><<<blocks(np, 256), 256, 0, st>>>(p, cur.a[0], cur.a[1], cur.a[2], h->keys[0],
+                                                  h->vals[0], np);
     LAUNCHED();
     const int nblk = (int)((np + SORT_TILE - 1) / SORT_TILE);
     const int passes = (h->key_bits + 7) / 8;
@@ -303,11 +373,18 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
 
 // Node pass over the layers deposited into (all layers if full), then roll the ranges.
 template <class T>
-mppic_status launch_finalize(mppic_handle* h, const KParams<T>& p, double* vs_out, bool full) {
+mppic_status launch_finalize(mppic_handle* h, const KParams<T>& p, double* vs_out, bool full,
+                             const KParams<T>* beds = nullptr) {
   Phase ph(h, PH_FINALIZE);
-  ph.launched(2);
   unsigned g = blocks(h->nnode, 256);
   if (g > 152u * 8u) g = 152u * 8u;
+  if (beds) {                  // a batch: every node of every bed
+    ph.launched(1);
+    k_finalize_b<T><<<g, 256, 0, h->stream>>>(beds, h->d_noff, h->nbeds, h->nnode);
+    LAUNCHED();
+    return MPPIC_OK;
+  }
+  ph.launched(2);
   k_finalize<T><<<g, 256, 0, h->stream>>>(p, vs_out, full ? 1 : 0);
   LAUNCHED();
   k_range_roll<<<1, 1, 0, h->stream>>>(h->zr);
@@ -324,25 +401,37 @@ mppic_status clear_volume_accumulator(mppic_handle* h) {
 
 template <class T>
 mppic_status launch_brick(mppic_handle* h, int mode, const KParams<T>& p, PArrays<T> src,
-                          PArrays<T> dst, int* cell_out, long long np) {
+                          PArrays<T> dst, int* cell_out, long long np,
+                          const KParams<T>* beds = nullptr) {
   const size_t sm = BrickSmem<T>::bytes;
   static bool attr_set[2] = {false, false};
+  static int resident[2] = {0, 0};
   if (!attr_set[mode]) {
-    if (mode == 0)
+    if (mode == 0) {
       CU(cudaFuncSetAttribute(k_brick<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    else
+      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_brick<T, 0>, BCELLS, sm));
+    } else {
       CU(cudaFuncSetAttribute(k_brick<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_brick<T, 1>, BCELLS, sm));
+    }
     attr_set[mode] = true;
   }
   if (h->nbricks == 0) return MPPIC_OK;
+  // persistent grid: the CTAs that fit on the GPU at once (or grid_factor per SM)
+  const int per_sm = h->grid_factor > 0 ? h->grid_factor : (resident[mode] > 0 ? resident[mode] : 1);
+  long long grid = (long long)per_sm * (h->nsm > 0 ? h->nsm : 1);
+  if (grid > h->nbricks) grid = h->nbricks;
+  CU(cudaMemsetAsync(h->wq, 0, sizeof(unsigned long long), h->stream));
   Phase ph(h, mode == 0 ? PH_DEPOSIT : PH_STEP);
   ph.launched();
   if (mode == 0)
-    k_brick<T, 0><<<(unsigned)h->nbricks, BCELLS, sm, h->stream>>>(p, src, dst, nullptr,
-                                                                   h->obj_part, np);
+    k_brick<T, 0><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
+                                                             h->wq, src, dst, nullptr,
+                                                             h->obj_part, np);
   else
-    k_brick<T, 1><<<(unsigned)h->nbricks, BCELLS, sm, h->stream>>>(p, src, dst, cell_out,
-                                                                   h->obj_part, np);
+    k_brick<T, 1><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
+                                                             h->wq, src, dst, cell_out,
+                                                             h->obj_part, np);
   LAUNCHED();
   return MPPIC_OK;
 }
@@ -431,9 +520,12 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
     src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
   }
   KParams<T> p = make_params<T>(h, gas);
-  mppic_status s = clear_volume_accumulator(h);
+  const KParams<T>* beds = nullptr;
+  mppic_status s = upload_beds<T>(h, gas, &beds);
   if (s) return s;
-  s = launch_brick<T>(h, 0, p, src, src, nullptr, pc->np);   // Vs of the current positions
+  s = clear_volume_accumulator(h);
+  if (s) return s;
+  s = launch_brick<T>(h, 0, p, src, src, nullptr, pc->np, beds);   // Vs of the current positions
   if (s) return s;
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   for (int it = 0; it < nsteps; ++it) {
@@ -446,21 +538,30 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
       s = save_checkpoint<T>(h, it / h->ckpt_every, src, np);
       if (s) return s;
     }
-    s = launch_finalize<T>(h, p, nullptr, false);
+    s = launch_finalize<T>(h, p, nullptr, false, beds);
     if (s) return s;
-    s = launch_brick<T>(h, 1, p, src, dst, it == nsteps - 1 ? pc->cell : nullptr, np);
+    s = launch_brick<T>(h, 1, p, src, dst, (it == nsteps - 1 && !beds) ? pc->cell : nullptr, np,
+                        beds);
     if (s) return s;
     src = dst;
     {
       Phase ph(h, PH_REDUCE);
       ph.launched();
-      k_obj_reduce<<<1, 1024, 0, h->stream>>>(h->obj_part, h->nbricks, area,
-                                              obj_out ? obj_out + 2 * it : h->obj_tmp);
+      if (beds)
+        k_obj_reduce_b<<<h->nbeds, 256, 0, h->stream>>>(
+            h->obj_part, h->d_boff, h->d_area, obj_out ? obj_out + 2LL * it * h->nbeds : h->obj_tmp);
+      else
+        k_obj_reduce<<<1, 1024, 0, h->stream>>>(h->obj_part, h->nbricks, area,
+                                                obj_out ? obj_out + 2 * it : h->obj_tmp);
       LAUNCHED();
     }
   }
-  if (nsteps == 0 && pc->cell && np > 0) {
-    k_bin<T><<<blocks(np, 256), 256, 0, h->stream>>>(p, dst.a[0], dst.a[1], dst.a[2], pc->cell, np);
+  if ((nsteps == 0 || beds) && pc->cell && np > 0) {
+    if (beds)
+      k_bin_b<T><<<blocks(np, 256), 256, 0, h->stream>>>(beds, h->d_poff, h->nbeds, dst.a[0],
+                                                          dst.a[1], dst.a[2], pc->cell, np);
+    else
+      k_bin<T><<<blocks(np, 256), 256, 0, h->stream>>>(p, dst.a[0], dst.a[1], dst.a[2], pc->cell, np);
     LAUNCHED();
   }
   h->order_on_caller = true;
@@ -595,7 +696,14 @@ mppic_status bin_impl(mppic_handle* h, mppic_parcels* pc, int do_sort) {
   }
   if (np > 0 && pc->cell) {
     KParams<T> p = make_params<T>(h, nullptr);
-    k_bin<T><<<blocks(np, 256), 256, 0, h->stream>>>(p, cur.a[0], cur.a[1], cur.a[2], pc->cell, np);
+    const KParams<T>* beds = nullptr;
+    mppic_status s = upload_beds<T>(h, nullptr, &beds);
+    if (s) return s;
+    if (beds)
+      k_bin_b<T><<<blocks(np, 256), 256, 0, h->stream>>>(beds, h->d_poff, h->nbeds, cur.a[0],
+                                                          cur.a[1], cur.a[2], pc->cell, np);
+    else
+      k_bin<T><<<blocks(np, 256), 256, 0, h->stream>>>(p, cur.a[0], cur.a[1], cur.a[2], pc->cell, np);
     LAUNCHED();
   }
   return MPPIC_OK;
@@ -633,37 +741,63 @@ int bits_for(long long n) {  // bits to represent values 0..n-1
 
 extern "C" {
 
+static mppic_status check_config(const mppic_config* c, const char* what, int index) {
+  mppic_handle* h = nullptr;
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1)
+    return fail(h, MPPIC_ERR_INVALID, "%s %d: grid %dx%dx%d must be at least 1 cell per axis", what,
+                index, c->nx, c->ny, c->nz);
+  if (!(c->dx > 0 && c->dy > 0 && c->dz > 0 && c->dt > 0))
+    return fail(h, MPPIC_ERR_INVALID, "%s %d: dx, dy, dz and dt must be positive", what, index);
+  if (!(c->rho_p > 0 && c->rho_g > 0 && c->mu_g > 0))
+    return fail(h, MPPIC_ERR_INVALID, "%s %d: densities and viscosity must be positive", what, index);
+  if (!(c->dscale > 0)) return fail(h, MPPIC_ERR_INVALID, "%s %d: dscale must be positive", what, index);
+  return MPPIC_OK;
+}
+
 mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* bed_parcel_offsets,
                           const mppic_config* per_bed, void* stream, mppic_handle** out) {
   mppic_handle* h = nullptr;
   if (!cfg || !out) return fail(h, MPPIC_ERR_INVALID, "cfg and out must not be NULL");
   *out = nullptr;
-  if (nbeds != 1 || bed_parcel_offsets || per_bed)
-    return fail(h, MPPIC_ERR_INVALID, "only nbeds == 1 is supported by this entry point");
-  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1)
-    return fail(h, MPPIC_ERR_INVALID, "grid %dx%dx%d must be at least 1 cell per axis", cfg->nx,
-                cfg->ny, cfg->nz);
-  if (!(cfg->dx > 0 && cfg->dy > 0 && cfg->dz > 0 && cfg->dt > 0))
-    return fail(h, MPPIC_ERR_INVALID, "dx, dy, dz and dt must be positive");
-  if (!(cfg->rho_p > 0 && cfg->rho_g > 0 && cfg->mu_g > 0))
-    return fail(h, MPPIC_ERR_INVALID, "densities and viscosity must be positive");
+  if (nbeds < 1) return fail(h, MPPIC_ERR_INVALID, "nbeds must be >= 1");
+  if (nbeds > 1 && (!bed_parcel_offsets || !per_bed))
+    return fail(h, MPPIC_ERR_INVALID, "a batch needs bed_parcel_offsets and per_bed");
   if (cfg->precision != 32 && cfg->precision != 64)
     return fail(h, MPPIC_ERR_INVALID, "precision must be 32 or 64, got %d", cfg->precision);
   if (cfg->sort_every < 0) return fail(h, MPPIC_ERR_INVALID, "sort_every must be >= 0");
-  const long long nnode = (long long)(cfg->nx + 1) * (cfg->ny + 1) * (cfg->nz + 1);
-  const long long nbx = (cfg->nx + BX - 1) / BX, nby = (cfg->ny + BY - 1) / BY,
-                  nbz = (cfg->nz + BZ - 1) / BZ;
-  const long long nkeys = nbx * nby * nbz * BCELLS;
-  if (nnode >= 0x7fffffffLL || nkeys >= 0x7fffffffLL)
-    return fail(h, MPPIC_ERR_INVALID, "grid too large: node or key count overflows int32");
+  std::vector<mppic_config> beds(nbeds);
+  for (int b = 0; b < nbeds; ++b) {
+    beds[b] = nbeds > 1 ? per_bed[b] : *cfg;
+    mppic_status s = check_config(&beds[b], "bed", b);
+    if (s) return s;
+  }
+  std::vector<long long> poff(nbeds + 1, 0), noff(nbeds + 1, 0), boff(nbeds + 1, 0);
+  for (int b = 0; b < nbeds; ++b) {
+    const mppic_config& c = beds[b];
+    if (nbeds > 1) {
+      poff[b + 1] = bed_parcel_offsets[b + 1];
+      if (bed_parcel_offsets[0] != 0 || poff[b + 1] < bed_parcel_offsets[b])
+        return fail(h, MPPIC_ERR_INVALID, "bed_parcel_offsets must start at 0 and not decrease");
+    }
+    noff[b + 1] = noff[b] + (long long)(c.nx + 1) * (c.ny + 1) * (c.nz + 1);
+    boff[b + 1] = boff[b] + (long long)((c.nx + BX - 1) / BX) * ((c.ny + BY - 1) / BY) * ((c.nz + BZ - 1) / BZ);
+  }
+  const long long nnode = noff[nbeds], nbricks = boff[nbeds], nkeys = nbricks * BCELLS;
+  if (nnode >= 0x7fffffffLL || nkeys >= 0x7fffffffLL || poff[nbeds] > 0x7fffffffLL)
+    return fail(h, MPPIC_ERR_INVALID, "grid too large: node, key or parcel count overflows int32");
   h = new (std::nothrow) mppic_handle();
   if (!h) return fail(nullptr, MPPIC_ERR_OOM, "host allocation failed");
-  h->cfg = *cfg;
+  h->cfg = beds[0];
+  h->cfg.precision = cfg->precision;
+  h->cfg.sort_every = cfg->sort_every;
+  h->nbeds = nbeds;
+  h->bed_cfg = beds;
+  h->poff = poff; h->noff = noff; h->boff = boff;
   h->stream = static_cast<cudaStream_t>(stream);
-  h->nx = cfg->nx; h->ny = cfg->ny; h->nz = cfg->nz;
-  h->nbx = (int)nbx; h->nby = (int)nby; h->nbz = (int)nbz;
+  h->nx = h->cfg.nx; h->ny = h->cfg.ny; h->nz = h->cfg.nz;
+  h->nbx = (h->nx + BX - 1) / BX; h->nby = (h->ny + BY - 1) / BY; h->nbz = (h->nz + BZ - 1) / BZ;
   h->nnode = nnode;
-  h->nbricks = nbx * nby * nbz;
+  h->nbricks = nbricks;
   h->nkeys = nkeys;
   h->key_bits = bits_for(nkeys);
   h->tsize = cfg->precision == 32 ? 4 : 8;
@@ -679,20 +813,43 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
     return true;
   };
   if (cudaGetDevice(&h->device) != cudaSuccess) s = fail(h, MPPIC_ERR_CUDA, "no CUDA device");
+  if (!s && cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+    s = fail(h, MPPIC_ERR_CUDA, "cannot read the SM count");
   if (!s && alloc((void**)&h->acc, sizeof(u64) * NQ * h->words * nnode) &&
       alloc(&h->fld, h->tsize * 5 * nnode) && alloc((void**)&h->cstart, sizeof(int) * (nkeys + 1)) &&
-      alloc((void**)&h->obj_part, sizeof(double) * 3 * h->nbricks) &&
-      alloc((void**)&h->obj_tmp, sizeof(double) * 2) && alloc((void**)&h->errs, sizeof(int)) &&
-      alloc((void**)&h->zr, sizeof(int) * 4) &&
+      alloc((void**)&h->obj_part, sizeof(double) * 3 * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->obj_tmp, sizeof(double) * 2 * nbeds) && alloc((void**)&h->errs, sizeof(int)) &&
+      alloc((void**)&h->zr, sizeof(int) * 4) && alloc((void**)&h->wq, sizeof(unsigned long long)) &&
       alloc((void**)&h->totals, sizeof(uint32_t) * 256)) {
     cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(u64) * NQ * h->words * nnode, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->errs, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fld, 0, h->tsize * 5 * nnode, h->stream);
     // no deposit yet; the first finalize covers every layer
-    const int zr0[4] = {1 << 30, -1, 0, cfg->nz};
+    const int zr0[4] = {1 << 30, -1, 0, h->cfg.nz};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->zr, zr0, sizeof(zr0), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && nbeds > 1) {
+      std::vector<int> brick_bed(nbricks);
+      std::vector<double> area(nbeds);
+      for (int b = 0; b < nbeds; ++b) {
+        for (long long g = boff[b]; g < boff[b + 1]; ++g) brick_bed[g] = b;
+        area[b] = beds[b].nx * beds[b].dx * beds[b].ny * beds[b].dy;
+      }
+      if (!alloc((void**)&h->d_poff, sizeof(long long) * (nbeds + 1)) ||
+          !alloc((void**)&h->d_noff, sizeof(long long) * (nbeds + 1)) ||
+          !alloc((void**)&h->d_boff, sizeof(long long) * (nbeds + 1)) ||
+          !alloc((void**)&h->d_brick_bed, sizeof(int) * (nbricks > 0 ? nbricks : 1)) ||
+          !alloc((void**)&h->d_area, sizeof(double) * nbeds)) {
+        e = cudaErrorMemoryAllocation;
+      } else {
+        e = cudaMemcpy(h->d_poff, poff.data(), sizeof(long long) * (nbeds + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_noff, noff.data(), sizeof(long long) * (nbeds + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_boff, boff.data(), sizeof(long long) * (nbeds + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_brick_bed, brick_bed.data(), sizeof(int) * nbricks, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_area, area.data(), sizeof(double) * nbeds, cudaMemcpyHostToDevice);
+      }
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) s = fail(h, MPPIC_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess && !s) s = fail(h, MPPIC_ERR_CUDA, "create: %s", cudaGetErrorString(e));
   }
   if (s) {
     snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
@@ -700,6 +857,13 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
     return s;
   }
   *out = h;
+  return MPPIC_OK;
+}
+
+mppic_status mppic_tune(mppic_handle* h, int grid_per_sm) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (grid_per_sm < 0 || grid_per_sm > 64) return fail(h, MPPIC_ERR_INVALID, "grid_per_sm out of range");
+  h->grid_factor = grid_per_sm;
   return MPPIC_OK;
 }
 
@@ -714,6 +878,7 @@ mppic_status mppic_bin(mppic_handle* h, mppic_parcels* parcels, int do_sort) {
 mppic_status mppic_deposit(mppic_handle* h, const mppic_parcels* parcels, const mppic_gas* gas,
                            double* Vs_out, void* fields_out) {
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (h->nbeds > 1) return fail(h, MPPIC_ERR_INVALID, "mppic_deposit takes a single-bed handle");
   mppic_status s = check_parcels(h, parcels);
   if (s) return s;
   const bool full = Vs_out != nullptr || fields_out != nullptr;
@@ -729,6 +894,7 @@ mppic_status mppic_deposit(mppic_handle* h, const mppic_parcels* parcels, const 
 mppic_status mppic_interp(mppic_handle* h, const mppic_parcels* parcels, const mppic_gas* gas,
                           void* out) {
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (h->nbeds > 1) return fail(h, MPPIC_ERR_INVALID, "mppic_interp takes a single-bed handle");
   mppic_status s = check_parcels(h, parcels);
   if (s) return s;
   if (!out && parcels->np > 0) return fail(h, MPPIC_ERR_INVALID, "out is NULL");
@@ -741,6 +907,9 @@ mppic_status mppic_step(mppic_handle* h, mppic_parcels* parcels, const mppic_gas
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
   mppic_status s = check_parcels(h, parcels);
   if (s) return s;
+  if (h->nbeds > 1 && parcels->np != h->poff[h->nbeds])
+    return fail(h, MPPIC_ERR_INVALID, "np=%lld does not match the batch's %lld parcels", parcels->np,
+                h->poff[h->nbeds]);
   if (nsteps < 0) return fail(h, MPPIC_ERR_INVALID, "nsteps must be >= 0");
   return h->cfg.precision == 32 ? step_impl<float>(h, parcels, gas, nsteps, obj_out)
                                 : step_impl<double>(h, parcels, gas, nsteps, obj_out);
@@ -748,6 +917,7 @@ mppic_status mppic_step(mppic_handle* h, mppic_parcels* parcels, const mppic_gas
 
 mppic_status mppic_set_params(mppic_handle* h, double drag_mult, double dscale, double u_in) {
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (h->nbeds > 1) return fail(h, MPPIC_ERR_INVALID, "mppic_set_params takes a single-bed handle");
   if (!(dscale > 0)) return fail(h, MPPIC_ERR_INVALID, "dscale must be positive");
   h->cfg.drag_mult = drag_mult;
   h->cfg.dscale = dscale;
@@ -757,6 +927,8 @@ mppic_status mppic_set_params(mppic_handle* h, double drag_mult, double dscale, 
 
 mppic_status mppic_checkpoint(mppic_handle* h, int every) {
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (h->nbeds > 1 && every != 0)
+    return fail(h, MPPIC_ERR_INVALID, "checkpointing takes a single-bed handle");
   if (every < 0) return fail(h, MPPIC_ERR_INVALID, "every must be >= 0");
   h->ckpt_every = every;
   h->last_nsteps = -1;
@@ -775,6 +947,7 @@ mppic_status mppic_backward(mppic_handle* h, const double* dL_d_dP_H, double* gr
 
 mppic_status mppic_drag_sums(mppic_handle* h, double* A, double* Bx, double* By, double* Bz) {
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (h->nbeds > 1) return fail(h, MPPIC_ERR_INVALID, "mppic_drag_sums takes a single-bed handle");
   return h->cfg.precision == 32 ? drag_impl<float>(h, A, Bx, By, Bz)
                                 : drag_impl<double>(h, A, Bx, By, Bz);
 }
@@ -843,6 +1016,8 @@ void mppic_destroy(mppic_handle* h) {
   for (void* c : h->ckpt) cudaFree(c);
   cudaFree(h->adj); cudaFree(h->adj_tmp); cudaFree(h->Vb); cudaFree(h->nadj); cudaFree(h->inv);
   cudaFree(h->work); cudaFree(h->seg); cudaFree(h->theta);
+  cudaFree(h->d_poff); cudaFree(h->d_noff); cudaFree(h->d_boff); cudaFree(h->d_brick_bed);
+  cudaFree(h->d_area); cudaFree(h->d_beds); cudaFree(h->wq);
   delete h;
 }
 
@@ -886,7 +1061,7 @@ __global__ void k_deposit_static(KParams<T> p, const T* __restrict__ x, const T*
       for (int a = 0; a < 2; ++a) {
         u64 fx[W];
         to_fixed(V * ((w[0][a] * w[1][b]) * w[2][cc]), p.mV, fx, p.errs);
-        acc_add(acc + node_id(p, c.i + a, c.j + b, c.k + cc), p.nnode, fx);
+        acc_add(acc + node_id(p, c.i + a, c.j + b, c.k + cc), p.nnode, fx);  // single bed
       }
 }
 
@@ -909,6 +1084,7 @@ mppic_status deposit_static_impl(const mppic_config* c, const mppic_parcels* pc,
   memset(&p, 0, sizeof(p));
   p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
   p.nnode = (long long)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+  p.nstride = p.nnode;
   const double hs[3] = {c->dx, c->dy, c->dz};
   for (int a = 0; a < 3; ++a) {
     p.inv_d[a] = 1.0 / hs[a];

@@ -91,7 +91,7 @@ __global__ void k_dep_simple(KParams<T> p, const T* __restrict__ x, const T* __r
       for (int a = 0; a < 2; ++a) {
         u64 fx[W];
         to_fixed(V * ((w[0][a] * w[1][b]) * w[2][cc]), p.mV, fx, p.errs);
-        acc_add(p.acc + node_id(p, c.i + a, c.j + b, c.k + cc), p.nnode, fx);
+        acc_add(p.acc + p.nbase + node_id(p, c.i + a, c.j + b, c.k + cc), p.nstride, fx);
       }
 }
 

@@ -42,6 +42,10 @@ struct KParams {
   int nbx, nby, nbz;
   long long nnode;
   long long nbricks;
+  // position of this bed in concatenated batch arrays (a single bed: 0, 0, nnode)
+  long long nbase;           // first node of the bed in the accumulator planes
+  long long bbase;           // first brick of the bed in the global brick (key) numbering
+  long long nstride;         // accumulator plane stride (nodes of all beds)
   double inv_d[3];           // fl64(1/h): binning multiplier
   float inv_f[3], inv_lo[3]; // FP32 split: inv_d ~= inv_f + inv_lo
   T invh[3];                 // 1/h in T (interpolant gradient)
@@ -611,7 +615,7 @@ __device__ __noinline__ void scatter_global(const KParams<T>& p, int cell, T x0,
           int q = q0 + v;
           u64 fx[W];
           to_fixed(vals[v] * Wq, q == 0 ? p.mV : p.mA, fx, p.errs);
-          acc_add(p.acc + (long long)(q * W) * p.nnode + gn, p.nnode, fx);
+          acc_add(p.acc + (long long)(q * W) * p.nstride + p.nbase + gn, p.nstride, fx);
         }
       }
 }
@@ -710,13 +714,16 @@ template <> struct Occupancy<double> { static constexpr int ctas = 2; };
 
 template <class T, int MODE>
 __global__ void __launch_bounds__(BCELLS, Occupancy<T>::ctas)
-k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out,
-        double* __restrict__ obj_part, long long np) {
+k_brick(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restrict__ brick_bed,
+        long long total_bricks, unsigned long long* __restrict__ work, PArrays<T> src,
+        PArrays<T> dst, int* __restrict__ cell_out, double* __restrict__ obj_part, long long np) {
   typedef BrickSmem<T> S;
   constexpr int W = S::W;
   constexpr int NC = S::NC;
   constexpr int SPAD = S::SPAD;
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ KParams<T> sp;                        // parameters of the current brick's bed
+  __shared__ long long s_brick;
   T* sf = reinterpret_cast<T*>(smem + S::fld);          // [TNODES][8]
   T* tile = reinterpret_cast<T*>(smem + S::acc);        // [NQ][TNODES]
   T* stage = reinterpret_cast<T*>(smem + S::stage);
@@ -736,8 +743,30 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const unsigned lanes_below = (1u << lane) - 1u;
-  const long long b = blockIdx.x;
-  const unsigned bu = blockIdx.x;
+  if (tid == 0) {
+    mbar_init(&mbar[0]);
+    mbar_init(&mbar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sflag[0] = 0;
+  }
+  const KParams<T>& p = sp;
+  int cur_bed = -1;
+  unsigned long long gk = 0;                     // chunks this CTA has staged (mbarrier parity)
+
+  // persistent loop: each iteration takes the next brick from the work counter
+  for (long long iter = 0; iter < total_bricks; ++iter) {
+  __syncthreads();
+  if (tid == 0) s_brick = (long long)atomicAdd(work, 1ull);
+  __syncthreads();
+  const long long b = s_brick;
+  if (b >= total_bricks) break;
+  const int bed = beds ? brick_bed[b] : 0;
+  if (bed != cur_bed) {
+    if (tid == 0) sp = beds ? beds[bed] : p0;
+    cur_bed = bed;
+    __syncthreads();
+  }
+  const unsigned bu = (unsigned)(b - p.bbase);   // brick within its bed
   const int bi = (int)(bu % (unsigned)p.nbx), bj = (int)((bu / (unsigned)p.nbx) % (unsigned)p.nby),
             bk = (int)(bu / ((unsigned)p.nbx * (unsigned)p.nby));
   const int bi0 = bi * BX, bj0 = bj * BY, bk0 = bk * BZ;
@@ -746,7 +775,7 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
 
   if (pstart == pend) {
     if (MODE == 1 && tid == 0) { obj_part[3 * b] = 0; obj_part[3 * b + 1] = 0; obj_part[3 * b + 2] = 0; }
-    return;
+    continue;
   }
 
   for (int e = tid; e < NQ * TNODES; e += BCELLS) tile[e] = 0;
@@ -763,12 +792,6 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
       sf[e] = v;
     }
   }
-  if (tid == 0) {
-    mbar_init(&mbar[0]);
-    mbar_init(&mbar[1]);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    sflag[0] = 0;
-  }
   __syncthreads();
 
   Fields<T> FG;
@@ -778,10 +801,10 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
   T o_dp = 0, o_hn = 0, o_vs = 0;
   int kdep_lo = 1 << 30, kdep_hi = -1;          // node layers this CTA deposits into
   const int nchunks = (pend - pstart + NC - 1) / NC;
-  if (tid == 0) issue_chunk(src, pstart, min(NC, pend - pstart), np, stage, &mbar[0]);
+  if (tid == 0) issue_chunk(src, pstart, min(NC, pend - pstart), np, stage + (gk & 1) * 8 * SPAD, &mbar[gk & 1]);
 
-  for (int kc = 0; kc < nchunks; ++kc) {
-    const int buf = kc & 1;
+  for (int kc = 0; kc < nchunks; ++kc, ++gk) {
+    const int buf = (int)(gk & 1);
     const long long c0 = (long long)pstart + (long long)kc * NC;
     const int cn = (int)min((long long)NC, (long long)pend - c0);
     const long long s0 = c0 & ~3LL;
@@ -792,7 +815,7 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
                   stage + (buf ^ 1) * 8 * SPAD, &mbar[buf ^ 1]);
     }
     // one thread waits for the chunk's bulk copies; the others sleep at the barrier below
-    if (tid == 0 && !mbar_wait(&mbar[buf], (uint32_t)((kc >> 1) & 1))) {
+    if (tid == 0 && !mbar_wait(&mbar[buf], (uint32_t)((gk >> 1) & 1))) {
       atomicOr(p.errs, ERR_TIMEOUT);
       sflag[0] = 1;
     }
@@ -808,7 +831,7 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
     }
     __syncthreads();
     if (sflag[0]) {             // a bulk copy never completed: drain what was issued and leave
-      if (tid == 0 && kc + 1 < nchunks) mbar_wait(&mbar[buf ^ 1], (uint32_t)(((kc + 1) >> 1) & 1));
+      if (tid == 0 && kc + 1 < nchunks) mbar_wait(&mbar[buf ^ 1], (uint32_t)(((gk + 1) >> 1) & 1));
       return;
     }
     // ---- phase A: one parcel per thread
@@ -1047,12 +1070,13 @@ k_brick(KParams<T> p, PArrays<T> src, PArrays<T> dst, int* __restrict__ cell_out
     if (v == T(0)) continue;
     u64 fx[W];
     to_fixed(v, q == 0 ? p.mV : p.mA, fx, p.errs);
-    acc_add(p.acc + (long long)(q * W) * p.nnode + node_id(p, i, j, k), p.nnode, fx);
+    acc_add(p.acc + (long long)(q * W) * p.nstride + p.nbase + node_id(p, i, j, k), p.nstride, fx);
   }
   if (MODE == 1) {
     __syncthreads();
     block_sum3(o_dp, o_hn, o_vs, reinterpret_cast<T*>(smem + S::rec), obj_part + 3 * b);
   }
+  }  // persistent loop
 }
 
 // a5: node fields from the deposited volume. Reads and clears the Vs accumulator and
@@ -1088,10 +1112,10 @@ __device__ __forceinline__ void finalize_node(const KParams<T>& p, int n, int i,
                                               double* vs_out) {
   constexpr int W = Words<T>::n;
   u64 fx[W];
-  for (int w = 0; w < W; ++w) { fx[w] = p.acc[(long long)w * p.nnode + n]; }
+  for (int w = 0; w < W; ++w) { fx[w] = p.acc[(long long)w * p.nstride + p.nbase + n]; }
   if (W == 1 && (long long)fx[0] >= (1ll << 62)) atomicOr(p.errs, ERR_RANGE);
   double Vs = from_fixed(fx, p.inv_mV);
-  for (int e = 0; e < NQ * W; ++e) p.acc[(long long)e * p.nnode + n] = 0;
+  for (int e = 0; e < NQ * W; ++e) p.acc[(long long)e * p.nstride + p.nbase + n] = 0;
   if (vs_out) vs_out[n] = Vs;
   double vn = p.vcell;
   if (i == 0 || i == p.nx) vn *= 0.5;
@@ -1121,7 +1145,7 @@ __global__ void k_drag_out(KParams<T> p, double* A, double* Bx, double* By, doub
   for (int q = 1; q < NQ; ++q) {
     if (!outs[q - 1]) continue;
     u64 fx[W];
-    for (int w = 0; w < W; ++w) fx[w] = p.acc[(long long)(q * W + w) * p.nnode + n];
+    for (int w = 0; w < W; ++w) fx[w] = p.acc[(long long)(q * W + w) * p.nstride + p.nbase + n];
     if (W == 1) {
       long long v = (long long)fx[0];
       if (v >= (1ll << 62) || v <= -(1ll << 62)) atomicOr(p.errs, ERR_RANGE);
@@ -1178,6 +1202,80 @@ __global__ void k_obj_reduce(const double* __restrict__ part, long long nb, doub
   if (t == 0) {
     obj[0] = s[0][0] / area;
     obj[1] = s[2][0] > 0 ? 2.0 * s[1][0] / s[2][0] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- batches --
+// Several independent beds share one sort and one launch of each kernel: their parcels,
+// nodes and bricks are concatenated; off arrays give each bed's first element.
+
+__device__ __forceinline__ int find_bed(const long long* __restrict__ off, int nbeds, long long x) {
+  int lo = 0, hi = nbeds;                        // largest b with off[b] <= x
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <class T>
+__global__ void k_keys_b(const KParams<T>* __restrict__ beds, const long long* __restrict__ poff,
+                         int nbeds, const T* __restrict__ x, const T* __restrict__ y,
+                         const T* __restrict__ z, uint32_t* __restrict__ key,
+                         uint32_t* __restrict__ val, long long np) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= np) return;
+  const KParams<T>& p = beds[find_bed(poff, nbeds, q)];
+  Cell3<T> c;
+  bin3(p, x[q], y[q], z[q], c);
+  key[q] = (uint32_t)(p.bbase * BCELLS) + brick_key(p, c.i, c.j, c.k);
+  val[q] = (uint32_t)q;
+}
+
+template <class T>
+__global__ void k_bin_b(const KParams<T>* __restrict__ beds, const long long* __restrict__ poff,
+                        int nbeds, const T* __restrict__ x, const T* __restrict__ y,
+                        const T* __restrict__ z, int* __restrict__ cell, long long np) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= np) return;
+  const KParams<T>& p = beds[find_bed(poff, nbeds, q)];
+  Cell3<T> c;
+  bin3(p, x[q], y[q], z[q], c);
+  cell[q] = cell_id(p, c.i, c.j, c.k);
+}
+
+template <class T>
+__global__ void k_finalize_b(const KParams<T>* __restrict__ beds, const long long* __restrict__ noff,
+                             int nbeds, long long total) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int bed = find_bed(noff, nbeds, g);
+    const KParams<T>& p = beds[bed];
+    const int n = (int)(g - noff[bed]);
+    const int nx1 = p.nx + 1, ny1 = p.ny + 1;
+    finalize_node(p, n, n % nx1, (n / nx1) % ny1, n / (nx1 * ny1), (double*)nullptr);
+  }
+}
+
+// Per-bed objectives: one CTA per bed sums the partials of its bricks in a fixed order.
+// obj[2*bed] = dP, obj[2*bed+1] = H.
+__global__ void k_obj_reduce_b(const double* __restrict__ part, const long long* __restrict__ boff,
+                               const double* __restrict__ area, double* __restrict__ obj) {
+  __shared__ double s[3][256];
+  const int bed = blockIdx.x, t = threadIdx.x;
+  double a = 0, b = 0, c = 0;
+  for (long long i = boff[bed] + t; i < boff[bed + 1]; i += blockDim.x) {
+    a += part[3 * i]; b += part[3 * i + 1]; c += part[3 * i + 2];
+  }
+  s[0][t] = a; s[1][t] = b; s[2][t] = c;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (t < off) { s[0][t] += s[0][t + off]; s[1][t] += s[1][t + off]; s[2][t] += s[2][t + off]; }
+    __syncthreads();
+  }
+  if (t == 0) {
+    obj[2 * bed] = s[0][0] / area[bed];
+    obj[2 * bed + 1] = s[2][0] > 0 ? 2.0 * s[1][0] / s[2][0] : 0.0;
   }
 }
 

@@ -101,6 +101,8 @@ def load():
         L.mppic_checkpoint.restype = st
         L.mppic_backward.argtypes = [H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.mppic_backward.restype = st
+        L.mppic_tune.argtypes = [H, ctypes.c_int]
+        L.mppic_tune.restype = st
         L.mppic_profile_enable.argtypes = [H, ctypes.c_int]
         L.mppic_profile_enable.restype = st
         L.mppic_profile_read.argtypes = [H, ctypes.POINTER(Profile)]
@@ -248,6 +250,10 @@ class Bed:
         self._ok(self.L.mppic_drag_sums(self.h, _ptr(A), _ptr(B[0]), _ptr(B[1]), _ptr(B[2])))
         return A, B
 
+    def tune(self, grid_per_sm: int):
+        """Persistent CTAs per SM of the step and deposit kernels (0 = all that fit)."""
+        self._ok(self.L.mppic_tune(self.h, int(grid_per_sm)))
+
     def set_params(self, drag_mult: float, dscale: float, u_in: float):
         """Set the three differentiable parameters (C, s_d, u_in) for later calls."""
         self._ok(self.L.mppic_set_params(self.h, float(drag_mult), float(dscale), float(u_in)))
@@ -315,3 +321,62 @@ class BedObjectives(torch.autograd.Function):
         g = grad_out.detach().double().cpu().tolist()
         grad = ctx.bed.backward(g[0], g[1])
         return torch.tensor(grad, dtype=torch.float64), None, None, None, None, None
+
+
+class Batch(Bed):
+    """Many independent beds advanced together by one handle (one sort, one persistent
+    launch per kernel and step). Parcels, and node arrays of the gas, are concatenated in
+    bed order; step() returns the (nsteps, nbeds, 2) objectives."""
+
+    def __init__(self, params_list, np_list, precision: int = 32, sort_every: int = 10,
+                 stream=None):
+        self.L = load()
+        self.precision = precision
+        self.dtype = dtype_of(precision)
+        self.nbeds = len(params_list)
+        cfgs = (Config * self.nbeds)(*[make_config(p, precision, sort_every) for p in params_list])
+        self.cfg = make_config(params_list[0], precision, sort_every)
+        offs = [0]
+        for n in np_list:
+            offs.append(offs[-1] + int(n))
+        self.offsets = offs
+        off_arr = (ctypes.c_longlong * (self.nbeds + 1))(*offs)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        h = ctypes.c_void_p()
+        st = self.L.mppic_create(ctypes.byref(self.cfg), self.nbeds, off_arr, cfgs,
+                                 ctypes.c_void_p(s.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            raise MppicError(st, self.L.mppic_last_error(None).decode())
+        self.h = h
+        self.nnode = int(self.L.mppic_num_nodes(h))
+        self.params = list(params_list)
+
+    def step(self, parcels: dict, gas, nsteps: int, obj=None):
+        ps = self._parcels(parcels)
+        gs = self._gas(gas)
+        if obj is None:
+            obj = torch.empty((max(nsteps, 1), self.nbeds, 2), dtype=torch.float64,
+                              device=parcels["x"].device)
+        self._ok(self.L.mppic_step(self.h, ctypes.byref(ps),
+                                   ctypes.byref(gs) if gs is not None else None,
+                                   int(nsteps), _ptr(obj)))
+        return obj[:nsteps]
+
+
+def concat_beds(beds, precision, device="cuda", with_pid=False):
+    """Concatenate synthetic beds (synth.Bed) into one parcel dict and one gas dict for Batch."""
+    import numpy as np
+    parcels = {k: np.concatenate([b.parcels[k] for b in beds]) for k in PARCEL_FIELDS}
+    dev = parcels_to_device(parcels, precision, device=device, with_pid=with_pid)
+    gas = None
+    if any(u is not None for b in beds for u in b.U):
+        U = []
+        for a in range(3):
+            parts = []
+            for b in beds:
+                nn = (b.params["nx"] + 1) * (b.params["ny"] + 1) * (b.params["nz"] + 1)
+                parts.append(b.U[a] if b.U[a] is not None else np.zeros(nn))
+            U.append(np.concatenate(parts))
+        gas = gas_to_device(U, None, precision, device=device)
+    return dev, gas
