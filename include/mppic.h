@@ -213,8 +213,19 @@ mppic_status mppic_deposit_static(const mppic_config *cfg, const mppic_parcels *
                                   double *Vs_out, void *stream);
 
 /* Launch tuning: the persistent step and deposit kernels use grid_per_sm CTAs per SM
- * (0 = as many as fit at once, the default). Results do not depend on it. */
-mppic_status mppic_tune(mppic_handle *h, int grid_per_sm);
+ * (0 = as many as fit at once, the default); sort_every >= 0 replaces the config's sort
+ * period (< 0 keeps it). Results do not depend on grid_per_sm; the sort period changes
+ * only the summation grouping (within the tolerances of the form). */
+mppic_status mppic_tune(mppic_handle *h, int grid_per_sm, int sort_every);
+
+/* mppic_step as one CUDA graph: the first call with a given set of arguments (array
+ * pointers, np, nsteps, obj_out, gas pointers) captures the whole nsteps-step sequence on
+ * the handle's stream and launches it; later calls with the same arguments relaunch the
+ * captured graph (one host call, no per-kernel launch cost). The captured sequence,
+ * including where it sorts, is replayed as is, so nsteps should be a multiple of the sort
+ * period. Changing parameters or tuning drops the graph. Not with checkpointing. */
+mppic_status mppic_step_graph(mppic_handle *h, mppic_parcels *parcels, const mppic_gas *gas,
+                              int nsteps, double *obj_out);
 
 /* Node count (nx+1)(ny+1)(nz+1) of the handle's bed (all beds of a batch). */
 long long mppic_num_nodes(const mppic_handle *h);

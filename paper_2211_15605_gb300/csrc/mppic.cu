@@ -36,6 +36,10 @@ struct mppic_handle {
   unsigned long long* wq = nullptr;              // persistent-kernel work counter
   int nsm = 0;
   int grid_factor = 0;                           // persistent CTAs per SM (0: resident maximum)
+  // captured step sequence (mppic_step_graph) and the arguments it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> gkey;
+  cudaStream_t cap_stream = nullptr;             // capture stream (the caller's may be the legacy one)
   cudaStream_t stream = nullptr;
   int device = 0;
   int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0;
@@ -110,12 +114,16 @@ mppic_status fail(mppic_handle* h, mppic_status s, const char* fmt, ...) {
   return s;
 }
 
+// A failed runtime call is reported through the status; the runtime's last-error state is
+// cleared so that the next launch check does not report it again.
 #define CU(call)                                                                          \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess)                                                                \
+    if (e_ != cudaSuccess) {                                                              \
+      cudaGetLastError();                                                                 \
       return fail(h, e_ == cudaErrorMemoryAllocation ? MPPIC_ERR_OOM : MPPIC_ERR_CUDA,    \
                   "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
+    }                                                                                     \
   } while (0)
 
 #define LAUNCHED()                                                                        \
@@ -731,6 +739,31 @@ mppic_status drag_impl(mppic_handle* h, double* A, double* Bx, double* By, doubl
   return MPPIC_OK;
 }
 
+// Everything a step call may do for the first time that is not allowed while a stream is
+// being captured: scratch allocation, kernel attributes, per-bed parameter upload.
+template <class T>
+mppic_status prepare_capture(mppic_handle* h, const mppic_parcels* pc, const mppic_gas* gas) {
+  mppic_status s = ensure_capacity(h, pc->np, pc->pid != nullptr);
+  if (s) return s;
+  const KParams<T>* beds = nullptr;
+  s = upload_beds<T>(h, gas, &beds);
+  if (s) return s;
+  const size_t sm = BrickSmem<T>::bytes;
+  CU(cudaFuncSetAttribute(k_brick<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  CU(cudaFuncSetAttribute(k_brick<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  KParams<T> p = make_params<T>(h, gas);
+  PArrays<T> none = caller_arrays<T>(pc);
+  // one zero-parcel launch of each brick kernel sets its one-time attributes and occupancy
+  const long long saved = h->nbricks;
+  h->nbricks = 0;
+  s = launch_brick<T>(h, 0, p, none, none, nullptr, 0, beds);
+  if (!s) s = launch_brick<T>(h, 1, p, none, none, nullptr, 0, beds);
+  h->nbricks = saved;
+  if (s) return s;
+  CU(cudaStreamSynchronize(h->stream));
+  return MPPIC_OK;
+}
+
 int bits_for(long long n) {  // bits to represent values 0..n-1
   int b = 0;
   while ((1LL << b) < n) ++b;
@@ -860,10 +893,12 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
   return MPPIC_OK;
 }
 
-mppic_status mppic_tune(mppic_handle* h, int grid_per_sm) {
+mppic_status mppic_tune(mppic_handle* h, int grid_per_sm, int sort_every) {
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
   if (grid_per_sm < 0 || grid_per_sm > 64) return fail(h, MPPIC_ERR_INVALID, "grid_per_sm out of range");
   h->grid_factor = grid_per_sm;
+  if (sort_every >= 0) h->cfg.sort_every = sort_every;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; h->gkey.clear(); }
   return MPPIC_OK;
 }
 
@@ -915,6 +950,61 @@ mppic_status mppic_step(mppic_handle* h, mppic_parcels* parcels, const mppic_gas
                                 : step_impl<double>(h, parcels, gas, nsteps, obj_out);
 }
 
+mppic_status mppic_step_graph(mppic_handle* h, mppic_parcels* parcels, const mppic_gas* gas,
+                              int nsteps, double* obj_out) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  mppic_status s = check_parcels(h, parcels);
+  if (s) return s;
+  if (nsteps < 1) return fail(h, MPPIC_ERR_INVALID, "nsteps must be >= 1");
+  if (h->ckpt_every > 0) return fail(h, MPPIC_ERR_INVALID, "mppic_step_graph does not checkpoint");
+  if (h->nbeds > 1 && parcels->np != h->poff[h->nbeds])
+    return fail(h, MPPIC_ERR_INVALID, "np=%lld does not match the batch's %lld parcels", parcels->np,
+                h->poff[h->nbeds]);
+  std::vector<const void*> key = {parcels->x, parcels->y, parcels->z, parcels->u, parcels->v,
+                                  parcels->w, parcels->d, parcels->omega, parcels->cell,
+                                  parcels->pid, (const void*)(intptr_t)parcels->np,
+                                  (const void*)(intptr_t)nsteps, obj_out};
+  for (int a = 0; a < 3; ++a) {
+    key.push_back(gas ? gas->U[a] : nullptr);
+    key.push_back(gas ? gas->gradp[a] : nullptr);
+  }
+  if (!h->gexec || key != h->gkey) {
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; h->gkey.clear(); }
+    s = h->cfg.precision == 32 ? prepare_capture<float>(h, parcels, gas)
+                               : prepare_capture<double>(h, parcels, gas);
+    if (s) return s;
+    if (!h->cap_stream) CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const bool prof = h->prof;
+    cudaStream_t user = h->stream;
+    h->prof = false;
+    h->stream = h->cap_stream;               // capture the sequence on the handle's own stream
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      h->stream = user; h->prof = prof; cudaGetLastError();
+      return fail(h, MPPIC_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    }
+    s = h->cfg.precision == 32 ? step_impl<float>(h, parcels, gas, nsteps, obj_out)
+                               : step_impl<double>(h, parcels, gas, nsteps, obj_out);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &graph);
+    h->stream = user;
+    h->prof = prof;
+    if (e != cudaSuccess) cudaGetLastError();
+    if (s) { if (graph) cudaGraphDestroy(graph); return s; }
+    if (e != cudaSuccess) return fail(h, MPPIC_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->gexec = nullptr;
+      cudaGetLastError();
+      return fail(h, MPPIC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    h->gkey = key;
+  }
+  CU(cudaGraphLaunch(h->gexec, h->stream));
+  return MPPIC_OK;
+}
+
 mppic_status mppic_set_params(mppic_handle* h, double drag_mult, double dscale, double u_in) {
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
   if (h->nbeds > 1) return fail(h, MPPIC_ERR_INVALID, "mppic_set_params takes a single-bed handle");
@@ -922,6 +1012,7 @@ mppic_status mppic_set_params(mppic_handle* h, double drag_mult, double dscale, 
   h->cfg.drag_mult = drag_mult;
   h->cfg.dscale = dscale;
   h->cfg.u_in = u_in;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; h->gkey.clear(); }
   return MPPIC_OK;
 }
 
@@ -1018,6 +1109,8 @@ void mppic_destroy(mppic_handle* h) {
   cudaFree(h->work); cudaFree(h->seg); cudaFree(h->theta);
   cudaFree(h->d_poff); cudaFree(h->d_noff); cudaFree(h->d_boff); cudaFree(h->d_brick_bed);
   cudaFree(h->d_area); cudaFree(h->d_beds); cudaFree(h->wq);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 

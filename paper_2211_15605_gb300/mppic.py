@@ -101,7 +101,10 @@ def load():
         L.mppic_checkpoint.restype = st
         L.mppic_backward.argtypes = [H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.mppic_backward.restype = st
-        L.mppic_tune.argtypes = [H, ctypes.c_int]
+        L.mppic_tune.argtypes = [H, ctypes.c_int, ctypes.c_int]
+        L.mppic_step_graph.argtypes = [H, ctypes.POINTER(Parcels), ctypes.POINTER(Gas),
+                                       ctypes.c_int, ctypes.c_void_p]
+        L.mppic_step_graph.restype = st
         L.mppic_tune.restype = st
         L.mppic_profile_enable.argtypes = [H, ctypes.c_int]
         L.mppic_profile_enable.restype = st
@@ -250,9 +253,20 @@ class Bed:
         self._ok(self.L.mppic_drag_sums(self.h, _ptr(A), _ptr(B[0]), _ptr(B[1]), _ptr(B[2])))
         return A, B
 
-    def tune(self, grid_per_sm: int):
-        """Persistent CTAs per SM of the step and deposit kernels (0 = all that fit)."""
-        self._ok(self.L.mppic_tune(self.h, int(grid_per_sm)))
+    def tune(self, grid_per_sm: int, sort_every: int = -1):
+        """Persistent CTAs per SM of the step and deposit kernels (0 = all that fit) and,
+        if >= 0, a new sort period."""
+        self._ok(self.L.mppic_tune(self.h, int(grid_per_sm), int(sort_every)))
+
+    def step_graph(self, parcels: dict, gas, nsteps: int, obj: torch.Tensor):
+        """nsteps steps as one captured CUDA graph (captured on the first call with these
+        arguments, relaunched afterwards). obj must be a preallocated device tensor."""
+        ps = self._parcels(parcels)
+        gs = self._gas(gas)
+        self._ok(self.L.mppic_step_graph(self.h, ctypes.byref(ps),
+                                         ctypes.byref(gs) if gs is not None else None,
+                                         int(nsteps), _ptr(obj)))
+        return obj
 
     def set_params(self, drag_mult: float, dscale: float, u_in: float):
         """Set the three differentiable parameters (C, s_d, u_in) for later calls."""

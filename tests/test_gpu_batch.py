@@ -65,3 +65,27 @@ def test_batch_matches_oracle():
             assert np.max(np.abs(got - ref[f])) <= 1e-12 * scale, (k, f)
         np.testing.assert_allclose(obj[:, k, 0], ex["obj"][:, 0], rtol=1e-11)
         np.testing.assert_allclose(obj[:, k, 1], ex["obj"][:, 1], rtol=1e-12)
+
+
+def test_graph_replay_equals_eager_and_tuning_keeps_results():
+    from paper_2211_15605_gb300 import tune
+    beds = _beds()
+    steps = 6
+    ref = mppic.Batch([b.params for b in beds], [b.np for b in beds], precision=32, sort_every=3)
+    d_ref, gas = mppic.concat_beds(beds, 32)
+    o_ref = ref.step(d_ref, gas, steps)
+    o_ref2 = ref.step(d_ref, gas, steps).clone()
+    ref.check()
+    g = mppic.Batch([b.params for b in beds], [b.np for b in beds], precision=32, sort_every=3)
+    d_g, gas_g = mppic.concat_beds(beds, 32)
+    obj = torch.empty((steps, len(beds), 2), dtype=torch.float64, device="cuda")
+    g.tune(1, 3)                                       # a different persistent grid
+    g.step_graph(d_g, gas_g, steps, obj)               # capture + launch
+    o1 = obj.clone()
+    g.step_graph(d_g, gas_g, steps, obj)               # relaunch
+    g.check()
+    for f in ("x", "y", "z", "u", "v", "w"):
+        assert torch.equal(d_g[f], d_ref[f]), f
+    assert torch.allclose(o1, o_ref, rtol=1e-12, atol=0) and torch.allclose(obj, o_ref2, rtol=1e-12, atol=0)
+    res = tune.autotune(g, d_g, gas_g, steps=3, grids=(0, 1), sorts=(3, 6))
+    assert res["best"] in res["ms_per_step"]
