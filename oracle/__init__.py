@@ -85,6 +85,9 @@ def lib():
             L.orc_step_tangent.argtypes = ([cp, ctypes.c_long] + [dp] * 8 + [dp] * 6
                                            + [ctypes.c_int, dp])
             L.orc_step_tangent.restype = ctypes.c_int
+            L.orc_step_sample.argtypes = ([cp, ctypes.c_long] + [dp] * 8 + [dp] * 3
+                                          + [ctypes.c_long, ctypes.POINTER(ctypes.c_long), dp, ip, dp])
+            L.orc_step_sample.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -223,3 +226,23 @@ def step_tangent(p, state: dict, nsteps: int, U=(None, None, None), gradp=None):
                                 _d(U[0]), _d(U[1]), _d(U[2]), _d(gps[0]), _d(gps[1]),
                                 _d(gps[2]), int(nsteps), _d(out))
     return out[:2].copy(), np.stack([out[2:5], out[5:8]]), int(st)
+
+
+def step_sample(p, state: dict, sample, U=(None, None, None)):
+    """One step of the sampled parcels with node fields deposited by all parcels.
+
+    Returns (new (6, ns) array of x, y, z, u, v, w; cell ids; f per parcel; status)."""
+    arrs = {k: _f64(state[k]) for k in ("x", "y", "z", "u", "v", "w", "d", "omega")}
+    idx = np.ascontiguousarray(sample, dtype=np.int64)
+    ns = idx.size
+    out = np.empty((6, ns))
+    cell = np.empty(ns, np.int32)
+    f = np.empty(ns)
+    U = [_f64(a) for a in U]
+    c = make_config(p)
+    st = lib().orc_step_sample(ctypes.byref(c), arrs["x"].size, *[_d(arrs[k]) for k in
+                               ("x", "y", "z", "u", "v", "w", "d", "omega")],
+                               _d(U[0]), _d(U[1]), _d(U[2]), ns,
+                               idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _d(out),
+                               cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(f))
+    return out, cell, f, int(st)

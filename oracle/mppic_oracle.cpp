@@ -478,6 +478,51 @@ int orc_step(const orc_config* c, long np, double* x, double* y, double* z, doub
   return status;
 }
 
+// One coupling step of the parcels listed in `sample` (indices into the np parcels), with
+// the node fields deposited by all np parcels: the same arithmetic as orc_step for those
+// parcels, for checking a large bed on a sample. Outputs per sampled parcel: new x, y, z,
+// u, v, w (6 arrays of ns), the new cell id, and its f = rho_p V D. Returns 0 or 4.
+int orc_step_sample(const orc_config* c, long np, const double* x, const double* y,
+                    const double* z, const double* u, const double* v, const double* w,
+                    const double* d, const double* om, const double* Ux, const double* Uy,
+                    const double* Uz, long ns, const long* sample, double* out6, int* cell,
+                    double* fout) {
+  Grid G(*c);
+  Params<double> P{c->drag_mult, c->dscale, c->u_in};
+  std::vector<double> Vs, eps_s, ug, tau;
+  deposit_volume(G, P, np, x, y, z, d, om, Vs);
+  const double* U[3] = {Ux, Uy, Uz};
+  const double* GP[3] = {nullptr, nullptr, nullptr};
+  node_fields(*c, G, P, Vs, U, eps_s, ug, tau);
+  int status = 0;
+  Stencil<double> st;
+  Interp<double> I;
+  for (long t = 0; t < ns; ++t) {
+    const long p = sample[t];
+    stencil(G, x[p], y[p], z[p], st);
+    interp(*c, st, eps_s, ug, tau, GP, I);
+    double up[3] = {u[p], v[p], w[p]};
+    double s[3] = {I.ug[0] - up[0], I.ug[1] - up[1], I.ug[2] - up[2]};
+    double D = wen_yu(*c, P, d[p], I.es, s);
+    double V = parcel_volume(d[p], om[p], P.sd);
+    fout[t] = c->rho_p * V * D;
+    double pos[3] = {x[p], y[p], z[p]};
+    for (int a = 0; a < 3; ++a) {
+      double acc = D * I.ug[a] + c->g[a] - I.gp[a] / c->rho_p;
+      if (I.es > 1e-12) acc = acc - I.gt[a] / (I.es * c->rho_p);
+      double un = (up[a] + c->dt * acc) / (1.0 + c->dt * D);
+      pos[a] = pos[a] + c->dt * un;
+      if (!reflect(pos[a], un, G.L[a], c->e_wall)) status = 4;
+      out6[a * ns + t] = pos[a];
+      out6[(3 + a) * ns + t] = un;
+    }
+    Stencil<double> sn;
+    stencil(G, pos[0], pos[1], pos[2], sn);
+    cell[t] = (int)sn.cell;
+  }
+  return status;
+}
+
 // Forward-mode oracle gradient. Runs nsteps steps carrying tangents with
 // respect to theta = (drag_mult, dscale, u_in) and returns
 //   out[0..1] = time averages of (dP, H) over the steps,

@@ -338,3 +338,18 @@ def test_tangent_matches_central_differences():
                 (name, o, grads[o, k], fd[o])
     _, ex, _ = oracle.step(p, st, steps, outputs=False)
     np.testing.assert_allclose(means, ex["obj"].mean(0), rtol=1e-14)
+
+
+def test_step_sample_agrees_with_full_step():
+    """The sampled-step routine computes, for the sampled parcels, exactly what the full
+    step computes (it shares the step's functions; this pins the sampling bookkeeping)."""
+    bed = synth.fourier_bed(n=3000, nx=8, ny=8, nz=16, nsteps=1)
+    synth.random_velocities(bed, 0.2, seed=12)
+    ref, ex, st = oracle.step(bed.params, bed.parcels, 1, U=bed.U)
+    assert st == 0
+    sample = np.array([0, 7, 123, 2999, 1500])
+    out, cell, f, st2 = oracle.step_sample(bed.params, bed.parcels, sample, U=bed.U)
+    assert st2 == 0
+    for a, k in enumerate(("x", "y", "z", "u", "v", "w")):
+        np.testing.assert_array_equal(out[a], ref[k][sample])
+    np.testing.assert_array_equal(cell, ex["cell"][sample])
