@@ -219,8 +219,8 @@ def run_gpu(args):
     shares = {k: round(v / max(sum(prof["ms"].values()), 1e-9), 4) for k, v in prof["ms"].items()}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "k_brick<float,1> (fused interp/drag/push/deposit)" if args.precision == 32
-                else "k_brick<double,1>", "peak_kind": peak_kind + " (hbm_gbs copy burst)",
+                "kernel": "k_cells<float,1> (fused interp/drag/push/deposit)" if args.precision == 32
+                else "k_cells<double,1>", "peak_kind": peak_kind + " (hbm_gbs copy burst)",
                 "bytes_per_launch": bpl, "ms_per_launch": round(step_ms, 5), "phase_ms": prof["ms"],
                 "phase_share": shares}
 
@@ -347,7 +347,7 @@ def run_batched(args):
     achieved = bpl / (step_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "k_brick<%s,1> (persistent, all beds)" % ("float" if args.precision == 32 else "double"),
+                "kernel": "k_cells<%s,1> (persistent, all beds)" % ("float" if args.precision == 32 else "double"),
                 "peak_kind": peak_kind + " (hbm_gbs copy burst)", "bytes_per_launch": bpl,
                 "ms_per_launch": round(step_ms, 5), "phase_ms": prof["ms"]}
     # end to end with host buffers: H2D of the parcel state, one graph replay, D2H

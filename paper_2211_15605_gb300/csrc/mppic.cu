@@ -364,12 +364,17 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
       ph.launched(3);
       src = 1 - src;
     }
-    k_gather<T><<<blocks(np, 256), 256, 0, st>>>(
-        cur, sorted_arrays<T>(h, cur.pid != nullptr, cur.tag != nullptr), h->vals[src], np);
-    LAUNCHED();
     k_cell_starts<<<blocks(h->nkeys + 1, 256), 256, 0, st>>>(h->keys[src], np, h->nkeys,
                                                              h->cstart);
-    ph.launched(3);
+    LAUNCHED();
+    // level layout within each group of 32 keys, into the value buffer the last pass freed
+    const long long ngroups = h->nkeys / 32;
+    k_level_perm<<<blocks(ngroups * 32, 256), 256, 0, st>>>(h->vals[src], h->cstart, ngroups,
+                                                             h->vals[1 - src]);
+    LAUNCHED();
+    k_gather<T><<<blocks(np, 256), 256, 0, st>>>(
+        cur, sorted_arrays<T>(h, cur.pid != nullptr, cur.tag != nullptr), h->vals[1 - src], np);
+    ph.launched(4);
   } else {
     CU(cudaMemsetAsync(h->cstart, 0, sizeof(int) * (h->nkeys + 1), st));
   }
@@ -408,19 +413,19 @@ mppic_status clear_volume_accumulator(mppic_handle* h) {
 }
 
 template <class T>
-mppic_status launch_brick(mppic_handle* h, int mode, const KParams<T>& p, PArrays<T> src,
+mppic_status launch_cells(mppic_handle* h, int mode, const KParams<T>& p, PArrays<T> src,
                           PArrays<T> dst, int* cell_out, long long np,
                           const KParams<T>* beds = nullptr) {
-  const size_t sm = BrickSmem<T>::bytes;
+  const size_t sm = CellSmem<T>::bytes;
   static bool attr_set[2] = {false, false};
   static int resident[2] = {0, 0};
   if (!attr_set[mode]) {
     if (mode == 0) {
-      CU(cudaFuncSetAttribute(k_brick<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_brick<T, 0>, BCELLS, sm));
+      CU(cudaFuncSetAttribute(k_cells<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_cells<T, 0>, BCELLS, sm));
     } else {
-      CU(cudaFuncSetAttribute(k_brick<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_brick<T, 1>, BCELLS, sm));
+      CU(cudaFuncSetAttribute(k_cells<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_cells<T, 1>, BCELLS, sm));
     }
     attr_set[mode] = true;
   }
@@ -433,11 +438,11 @@ mppic_status launch_brick(mppic_handle* h, int mode, const KParams<T>& p, PArray
   Phase ph(h, mode == 0 ? PH_DEPOSIT : PH_STEP);
   ph.launched();
   if (mode == 0)
-    k_brick<T, 0><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
+    k_cells<T, 0><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
                                                              h->wq, src, dst, nullptr,
                                                              h->obj_part, np);
   else
-    k_brick<T, 1><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
+    k_cells<T, 1><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
                                                              h->wq, src, dst, cell_out,
                                                              h->obj_part, np);
   LAUNCHED();
@@ -460,7 +465,7 @@ mppic_status deposit_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_
   KParams<T> p = make_params<T>(h, gas);
   mppic_status s = clear_volume_accumulator(h);
   if (s) return s;
-  s = launch_brick<T>(h, 0, p, src, src, nullptr, pc->np);
+  s = launch_cells<T>(h, 0, p, src, src, nullptr, pc->np);
   if (s) return s;
   s = launch_finalize<T>(h, p, vs_out, full);
   if (s) return s;
@@ -533,7 +538,7 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   if (s) return s;
   s = clear_volume_accumulator(h);
   if (s) return s;
-  s = launch_brick<T>(h, 0, p, src, src, nullptr, pc->np, beds);   // Vs of the current positions
+  s = launch_cells<T>(h, 0, p, src, src, nullptr, pc->np, beds);   // Vs of the current positions
   if (s) return s;
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   for (int it = 0; it < nsteps; ++it) {
@@ -548,7 +553,7 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
     }
     s = launch_finalize<T>(h, p, nullptr, false, beds);
     if (s) return s;
-    s = launch_brick<T>(h, 1, p, src, dst, (it == nsteps - 1 && !beds) ? pc->cell : nullptr, np,
+    s = launch_cells<T>(h, 1, p, src, dst, (it == nsteps - 1 && !beds) ? pc->cell : nullptr, np,
                         beds);
     if (s) return s;
     src = dst;
@@ -748,16 +753,16 @@ mppic_status prepare_capture(mppic_handle* h, const mppic_parcels* pc, const mpp
   const KParams<T>* beds = nullptr;
   s = upload_beds<T>(h, gas, &beds);
   if (s) return s;
-  const size_t sm = BrickSmem<T>::bytes;
-  CU(cudaFuncSetAttribute(k_brick<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  CU(cudaFuncSetAttribute(k_brick<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const size_t sm = CellSmem<T>::bytes;
+  CU(cudaFuncSetAttribute(k_cells<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  CU(cudaFuncSetAttribute(k_cells<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   KParams<T> p = make_params<T>(h, gas);
   PArrays<T> none = caller_arrays<T>(pc);
-  // one zero-parcel launch of each brick kernel sets its one-time attributes and occupancy
+  // one zero-parcel launch of each cell kernel sets its one-time attributes and occupancy
   const long long saved = h->nbricks;
   h->nbricks = 0;
-  s = launch_brick<T>(h, 0, p, none, none, nullptr, 0, beds);
-  if (!s) s = launch_brick<T>(h, 1, p, none, none, nullptr, 0, beds);
+  s = launch_cells<T>(h, 0, p, none, none, nullptr, 0, beds);
+  if (!s) s = launch_cells<T>(h, 1, p, none, none, nullptr, 0, beds);
   h->nbricks = saved;
   if (s) return s;
   CU(cudaStreamSynchronize(h->stream));

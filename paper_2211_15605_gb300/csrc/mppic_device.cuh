@@ -474,102 +474,38 @@ __global__ void k_gather(PArrays<T> src, PArrays<T> dst, const uint32_t* __restr
   if (src.tag) dst.tag[q] = src.tag[s];
 }
 
-// ------------------------------------------------------------ brick CTA --
+// ------------------------------------------------------------ level layout --
 
-template <class T> struct Chunk;                          // parcels per CTA chunk
-template <> struct Chunk<float> { static constexpr int n = 512; };
-template <> struct Chunk<double> { static constexpr int n = 256; };
+constexpr unsigned FULL = 0xffffffffu;
 
-constexpr size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-// Shared-memory layout of the brick kernels (every section 128-byte aligned; the staging
-// rows must be 16-byte aligned for the bulk copies).
-template <class T>
-struct BrickSmem {
-  static constexpr int W = Words<T>::n;
-  static constexpr int NC = Chunk<T>::n;
-  static constexpr int SPAD = NC + 8;                                    // staging row length
-  static constexpr size_t fld = 0;                                       // [TNODES][8] T (AoS)
-  static constexpr size_t acc = rup(fld + sizeof(T) * 8 * TNODES, 128);  // [NQ][TNODES] T
-  static constexpr size_t stage = rup(acc + sizeof(T) * NQ * TNODES, 128);  // [2][8][SPAD] T
-  static constexpr size_t rec = rup(stage + sizeof(T) * 2 * 8 * SPAD, 128);
-  // records: f, xi_old[3], xi_new[3] (7 T), old and new cell (2 int), local key (int)
-  static constexpr size_t cells = rup(rec + sizeof(T) * 7 * NC + sizeof(int) * 3 * NC, 128);
-  // list of records not in their sorted cell [NC], and each cell's record range in the
-  // chunk [2][BCELLS]
-  static constexpr size_t misc = rup(cells + sizeof(int) * (NC + 2 * BCELLS), 128);
-  // 2 mbarriers (16 B) + 16 ints: abort flag, drift-list length, first and last cell of
-  // the chunk, per-warp drift counts
-  static constexpr size_t bytes = misc + 16 + 16 * sizeof(int);
-};
-
-// ---- bulk-copy staging (cp.async.bulk with an mbarrier, bounded waits)
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* m) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(m)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect(uint64_t* m, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)),
-               "r"(bytes)
-               : "memory");
-}
-
-// Waits for the given phase parity; gives up after a bounded number of polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
-  const uint32_t a = smem_addr(m);
-  for (int it = 0; it < (1 << 16); ++it) {
-    uint32_t done;
-    // the suspend-time hint (ns) lets the thread sleep in the instruction instead of polling
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity), "r"(20000u)
-        : "memory");
-    if (done) return true;
+// The step kernel runs one thread per cell, one warp per group of 32 consecutive keys
+// (32 cells of a brick). Within each group the parcels are laid out by level: level r
+// holds the r-th parcel (in sorted order) of every cell of the group that has more than
+// r parcels, in cell order. Then the warp's r-th iteration reads one contiguous run.
+// perm_out[level position] = perm_in[cell-sorted position]; one warp per group.
+__global__ void k_level_perm(const uint32_t* __restrict__ perm_in, const int* __restrict__ start,
+                             long long ngroups, uint32_t* __restrict__ perm_out) {
+  const long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= ngroups) return;                      // whole warps leave together
+  const long long key = g * 32 + lane;
+  const int cs = start[key];
+  const int n = start[key + 1] - cs;
+  const int nmax = __reduce_max_sync(FULL, n);
+  const unsigned below = (1u << lane) - 1u;
+  int off = __shfl_sync(FULL, cs, 0);
+  for (int r = 0; r < nmax; ++r) {
+    const bool act = n > r;
+    const unsigned bal = __ballot_sync(FULL, act);
+    if (act) perm_out[off + __popc(bal & below)] = perm_in[cs + r];
+    off += __popc(bal);
   }
-  return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(m))
-      : "memory");
-}
-
-// The staged element range of a chunk [c0, c0+cn): [c0 & ~3, end) is copied in bulk, where
-// end is c0+cn rounded up to 4 elements but not past the last full group of 4 of the
-// array (np), so no byte beyond the caller's array is read. Elements from end to c0+cn
-// are loaded with plain loads.
-__device__ __forceinline__ long long bulk_end(long long c0, int cn, long long np) {
-  long long s0 = c0 & ~3LL;
-  long long e = (c0 + cn + 3) & ~3LL;
-  long long lim = np & ~3LL;
-  if (e > lim) e = lim;
-  if (e < s0) e = s0;
-  return e;
-}
-
-template <class T>
-__device__ void issue_chunk(const PArrays<T>& src, long long c0, int cn, long long np, T* stage_buf,
-                            uint64_t* m) {
-  constexpr int SPAD = BrickSmem<T>::SPAD;
-  const long long s0 = c0 & ~3LL;
-  const uint32_t bytes = (uint32_t)((bulk_end(c0, cn, np) - s0) * sizeof(T));
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect(m, 8u * bytes);
-  if (bytes)
-    for (int f = 0; f < 8; ++f) bulk_g2s(stage_buf + f * SPAD, src.a[f] + s0, bytes, m);
 }
 
 // ---- math of the step: full precision in the FP64 form, CUDA's fast intrinsics in FP32.
+
+constexpr size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
 __device__ __forceinline__ float fpow(float a, float b) { return __powf(a, b); }
 __device__ __forceinline__ double fpow(double a, double b) { return pow(a, b); }
 __device__ __forceinline__ float frcp(float a) { return __fdividef(1.0f, a); }
@@ -593,33 +529,6 @@ __device__ __forceinline__ T wen_yu_fast(const KParams<T>& p, T d, T es, const T
   return p.kD2 * smag * e165 * inv_de;
 }
 
-// Adds the fixed-point contributions of one parcel (values at the 8 corners of cell (i,j,k)
-// with in-cell coordinates xi) straight to the global accumulators. Used for parcels whose
-// cell is not their sorted cell (they drifted since the last sort, or moved this step).
-template <class T, int NV>
-__device__ __noinline__ void scatter_global(const KParams<T>& p, int cell, T x0, T x1, T x2, T v0,
-                                            T v1, T v2, T v3) {
-  constexpr int W = Words<T>::n;
-  int i, j, k;
-  decode_cell(p, cell, i, j, k);
-  const T vals[4] = {v0, v1, v2, v3};
-  const T w[3][2] = {{T(1) - x0, x0}, {T(1) - x1, x1}, {T(1) - x2, x2}};
-  const int q0 = NV == 1 ? 0 : 1;
-  for (int c = 0; c < 2; ++c)
-    for (int b = 0; b < 2; ++b)
-      for (int a = 0; a < 2; ++a) {
-        T Wq = (w[0][a] * w[1][b]) * w[2][c];
-        long long gn = node_id(p, i + a, j + b, k + c);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          int q = q0 + v;
-          u64 fx[W];
-          to_fixed(vals[v] * Wq, q == 0 ? p.mV : p.mA, fx, p.errs);
-          acc_add(p.acc + (long long)(q * W) * p.nstride + p.nbase + gn, p.nstride, fx);
-        }
-      }
-}
-
 // Deterministic block reduction of three per-thread values in T, in thread order.
 template <class T>
 __device__ void block_sum3(T a, T b, T c, T* sm, double* out) {
@@ -637,20 +546,28 @@ __device__ void block_sum3(T a, T b, T c, T* sm, double* out) {
   if (t == 0) { out[0] = (double)sm[0]; out[1] = (double)sm[BCELLS]; out[2] = (double)sm[2 * BCELLS]; }
 }
 
-// Node values of corner n of the AoS field tile: eps_s, u_g[3], tau, grad p[3].
+// The brick's node-field tile is stored as planes of 16-byte vectors: plane k holds fields
+// VW*k .. VW*k+VW-1 of every node (VW = 4 floats or 2 doubles), node-major, so the 8
+// lanes of a quarter-warp (8 consecutive nodes along x) read 128 contiguous bytes.
+// Fields: eps_s, u_g[3], tau, grad p[3].
+template <class T> struct TileVec;
+template <> struct TileVec<float> { static constexpr int n = 4; };
+template <> struct TileVec<double> { static constexpr int n = 2; };
+
 __device__ __forceinline__ void tile_node(const float* t, int n, float (&v)[8]) {
-  const float4 a = *reinterpret_cast<const float4*>(t + 8 * n);
-  const float4 b = *reinterpret_cast<const float4*>(t + 8 * n + 4);
+  const float4 a = *reinterpret_cast<const float4*>(t + 4 * n);
+  const float4 b = *reinterpret_cast<const float4*>(t + 4 * (TNODES + n));
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 __device__ __forceinline__ void tile_node(const double* t, int n, double (&v)[8]) {
-  for (int f = 0; f < 8; f += 2) {
-    const double2 a = *reinterpret_cast<const double2*>(t + 8 * n + f);
-    v[f] = a.x; v[f + 1] = a.y;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = *reinterpret_cast<const double2*>(t + 2 * (k * TNODES + n));
+    v[2 * k] = a.x; v[2 * k + 1] = a.y;
   }
 }
 
-// Interpolation at one parcel from the brick's AoS field tile (corner (0,0,0) at tile node
+// Interpolation at one parcel from the brick's node-field tile (corner (0,0,0) at tile node
 // base). The gradient of the trilinear interpolant of tau is formed from differences across
 // the cell faces: d/dx = (1/dx) sum_{b,c} (tau_1bc - tau_0bc) w_y,b w_z,c, and likewise.
 template <class T>
@@ -694,66 +611,119 @@ __device__ __forceinline__ void interp_tile(const KParams<T>& p, const T* t, int
   r.gt[2] = gz * p.invh[2];
 }
 
-// The brick kernel. One CTA owns the parcels of one brick (its range of the sorted order).
+// ------------------------------------------------------------ cell kernel --
+
+// Shared memory of the cell kernels (sections 128-byte aligned).
+constexpr int PSTAGES = 5;                       // parcel levels in flight per thread
+template <class T>
+struct CellSmem {
+  static constexpr int W = Words<T>::n;
+  static constexpr size_t fld = 0;                                         // node-field tile
+  static constexpr size_t fx = rup(fld + sizeof(T) * 8 * TNODES, 128);     // [NQ][W][TNODES] u64
+  static constexpr size_t tile = rup(fx + sizeof(u64) * NQ * W * TNODES, 128);  // [NQ][TNODES] T
+  static constexpr size_t red = rup(tile + sizeof(T) * NQ * TNODES, 128);  // [3][BCELLS] T
+  static constexpr size_t pre = rup(red + sizeof(T) * 3 * BCELLS, 128);    // [PSTAGES][8][BCELLS] T
+  static constexpr size_t bytes = pre + sizeof(T) * PSTAGES * 8 * BCELLS;
+};
+
+// Asynchronous copy of one parcel value into this thread's prefetch slot.
+__device__ __forceinline__ void cp_async(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Adds NV values at the 8 corners of cell (i,j,k) with in-cell coordinates x0..x2 in exact
+// fixed point, starting at quantity q0 (0 = Vs, 1 = A, then Bx, By, Bz): into the brick's
+// shared tile if the cell is in the brick (i0, j0, k0 = its first cell), else into the
+// global accumulators. Integer additions commute, so the order of these calls does not
+// change any sum. Used for parcels that are not in their sorted cell.
+template <class T, int NV>
+__device__ __noinline__ void deposit_foreign(const KParams<T>& p, u64* fx, int i0, int j0, int k0,
+                                             int i, int j, int k, T x0, T x1, T x2, int q0,
+                                             T v0, T v1, T v2, T v3) {
+  constexpr int W = Words<T>::n;
+  const T vals[4] = {v0, v1, v2, v3};
+  const T w[3][2] = {{T(1) - x0, x0}, {T(1) - x1, x1}, {T(1) - x2, x2}};
+  const int ti = i - i0, tj = j - j0, tk = k - k0;
+  const bool in = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
+  for (int q = 0; q < 8; ++q) {
+    const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
+    const T Wq = (w[0][a] * w[1][b]) * w[2][c];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int qq = q0 + v;
+      u64 f[W];
+      to_fixed(vals[v] * Wq, qq == 0 ? p.mV : p.mA, f, p.errs);
+      if (in)
+        acc_add(fx + (qq * W) * TNODES + (ti + a) + TX * ((tj + b) + TY * (tk + c)), TNODES, f);
+      else
+        acc_add(p.acc + (long long)(qq * W) * p.nstride + p.nbase + node_id(p, i + a, j + b, k + c),
+                p.nstride, f);
+    }
+  }
+}
+
+// Trilinear corner weights of in-cell coordinates xi, corner q = a + 2b + 4c.
+template <class T>
+__device__ __forceinline__ void corner_weights(const T (&xi)[3], T (&Wq)[8]) {
+  const T w[3][2] = {{T(1) - xi[0], xi[0]}, {T(1) - xi[1], xi[1]}, {T(1) - xi[2], xi[2]}};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) Wq[q] = (w[0][q & 1] * w[1][(q >> 1) & 1]) * w[2][q >> 2];
+}
+
+// The cell kernel. One CTA owns one brick (taken from a work counter: persistent grid);
+// thread t owns local cell t, warp w the group of cells 32w..32w+31, whose parcels are
+// stored by level (k_level_perm). The warp's r-th iteration processes the r-th parcel of
+// each of its cells that has one, one per thread, with coalesced loads and stores.
 // MODE 0: deposit the solids volume of the current positions.
-// MODE 1: one full step for those parcels (interp, drag, drag sums, objectives, push,
-// walls, re-bin), depositing the solids volume of the new positions for the next step.
-// src/dst may be the same arrays; if not, the read-only arrays are copied too.
-//
-// Per chunk of NC parcels: the 8 parcel arrays are bulk-copied into shared memory (the
-// next chunk's copy is in flight while this one is processed); phase A runs one parcel per
-// thread and leaves a record; phase B, one thread per cell, sums the records of its cell in
-// registers and adds the sums to a shared node tile in 8 corner phases separated by
-// barriers, so no two threads touch a node in the same phase and the order is fixed.
-// Records whose cell is not their sorted cell go to the global accumulators in exact
-// fixed point. At the end of the brick the tile is converted to fixed point and added to
-// the global accumulators.
-template <class T> struct Occupancy;
-template <> struct Occupancy<float> { static constexpr int ctas = 2; };
-template <> struct Occupancy<double> { static constexpr int ctas = 2; };
+// MODE 1: one full step (interp from a shared node-field tile, drag, drag sums,
+// objectives, push, walls, re-bin), depositing the solids volume of the new positions
+// for the next step. src/dst may be the same arrays; if not, the read-only arrays are
+// copied too.
+// A thread sums the contributions of its own cell's parcels (old position for the drag
+// sums, new position for the volume) at the cell's 8 corners in registers: 40 sums,
+// converted once per brick to exact fixed point and added to a shared node tile. A
+// parcel that is not in its sorted cell (it drifted since the last sort, or moved this
+// step) adds its contributions in fixed point straight to the shared tile (or, outside
+// the brick, to the global accumulators). The tile is flushed to the global accumulators
+// once per brick. No step waits on another thread except at the brick's start and end.
+template <class T> struct CellOccupancy;
+template <> struct CellOccupancy<float> { static constexpr int ctas = 2; };
+template <> struct CellOccupancy<double> { static constexpr int ctas = 1; };
 
 template <class T, int MODE>
-__global__ void __launch_bounds__(BCELLS, Occupancy<T>::ctas)
-k_brick(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restrict__ brick_bed,
+__global__ void __launch_bounds__(BCELLS, CellOccupancy<T>::ctas)
+k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restrict__ brick_bed,
         long long total_bricks, unsigned long long* __restrict__ work, PArrays<T> src,
         PArrays<T> dst, int* __restrict__ cell_out, double* __restrict__ obj_part, long long np) {
-  typedef BrickSmem<T> S;
+  typedef CellSmem<T> S;
   constexpr int W = S::W;
-  constexpr int NC = S::NC;
-  constexpr int SPAD = S::SPAD;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ KParams<T> sp;                        // parameters of the current brick's bed
   __shared__ long long s_brick;
-  T* sf = reinterpret_cast<T*>(smem + S::fld);          // [TNODES][8]
-  T* tile = reinterpret_cast<T*>(smem + S::acc);        // [NQ][TNODES]
-  T* stage = reinterpret_cast<T*>(smem + S::stage);
-  T* rf = reinterpret_cast<T*>(smem + S::rec);
-  T* rxo = rf + NC;                              // [3][NC]
-  T* rxn = rxo + 3 * NC;                         // [3][NC]
-  int* rco = reinterpret_cast<int*>(rxn + 3 * NC);
-  int* rcn = rco + NC;
-  int* rkey = rcn + NC;                          // local cell of the current position, or BCELLS
-  int* drift = reinterpret_cast<int*>(smem + S::cells);  // [NC] records not in their sorted cell
-  int* cr0 = drift + NC;                         // [BCELLS] chunk record range of each sorted cell
-  int* cr1 = cr0 + BCELLS;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::misc);
-  int* sflag = reinterpret_cast<int*>(smem + S::misc + 16);
-  // sflag: [0] abort, [1] drift-list length, [2] first cell, [3] last cell, [4..11] per-warp drift counts
+  T* sf = reinterpret_cast<T*>(smem + S::fld);     // node-field tile (planes)
+  T* pre = reinterpret_cast<T*>(smem + S::pre);    // [PSTAGES][8][BCELLS] prefetched parcels
+  u64* fx = reinterpret_cast<u64*>(smem + S::fx);  // [NQ][W][TNODES] parcels off their sorted cell
+  T* tile = reinterpret_cast<T*>(smem + S::tile);  // [NQ][TNODES] sums of the cells' own parcels
+  T* red = reinterpret_cast<T*>(smem + S::red);
 
   const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const unsigned lanes_below = (1u << lane) - 1u;
-  if (tid == 0) {
-    mbar_init(&mbar[0]);
-    mbar_init(&mbar[1]);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    sflag[0] = 0;
-  }
+  const int lane = tid & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int lti = tid % BX, ltj = (tid / BX) % BY, ltk = tid / (BX * BY);
   const KParams<T>& p = sp;
   int cur_bed = -1;
-  unsigned long long gk = 0;                     // chunks this CTA has staged (mbarrier parity)
+  const bool copy_ro = src.a[0] != dst.a[0];
 
-  // persistent loop: each iteration takes the next brick from the work counter
   for (long long iter = 0; iter < total_bricks; ++iter) {
   __syncthreads();
   if (tid == 0) s_brick = (long long)atomicAdd(work, 1ull);
@@ -767,315 +737,218 @@ k_brick(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     __syncthreads();
   }
   const unsigned bu = (unsigned)(b - p.bbase);   // brick within its bed
-  const int bi = (int)(bu % (unsigned)p.nbx), bj = (int)((bu / (unsigned)p.nbx) % (unsigned)p.nby),
-            bk = (int)(bu / ((unsigned)p.nbx * (unsigned)p.nby));
-  const int bi0 = bi * BX, bj0 = bj * BY, bk0 = bk * BZ;
+  const int bi0 = (int)(bu % (unsigned)p.nbx) * BX;
+  const int bj0 = (int)((bu / (unsigned)p.nbx) % (unsigned)p.nby) * BY;
+  const int bk0 = (int)(bu / ((unsigned)p.nbx * (unsigned)p.nby)) * BZ;
   const long long kbase = b * BCELLS;
-  const int pstart = p.cstart[kbase], pend = p.cstart[kbase + BCELLS];
-
-  if (pstart == pend) {
+  if (p.cstart[kbase] == p.cstart[kbase + BCELLS]) {
     if (MODE == 1 && tid == 0) { obj_part[3 * b] = 0; obj_part[3 * b + 1] = 0; obj_part[3 * b + 2] = 0; }
     continue;
   }
 
-  for (int e = tid; e < NQ * TNODES; e += BCELLS) tile[e] = 0;
+  const int nq = MODE == 1 ? NQ : 1;
+  for (int e = tid; e < nq * W * TNODES; e += BCELLS) fx[e] = 0;
+  for (int e = tid; e < nq * TNODES; e += BCELLS) tile[e] = 0;
   if (MODE == 1) {
+    // asynchronous copies, all in flight at once; absent nodes and fields are zero
+    constexpr int VW = TileVec<T>::n;
     for (int e = tid; e < 8 * TNODES; e += BCELLS) {
-      int tn = e >> 3, f = e & 7;
-      int ti = tn % TX, tj = (tn / TX) % TY, tk = tn / (TX * TY);
-      int i = bi0 + ti, j = bj0 + tj, k = bk0 + tk;
-      T v = 0;
+      const int tn = e / 8, f = e % 8;
+      const int i = bi0 + tn % TX, j = bj0 + (tn / TX) % TY, k = bk0 + tn / (TX * TY);
+      T* dstv = sf + VW * ((f / VW) * TNODES + tn) + f % VW;
       if (i <= p.nx && j <= p.ny && k <= p.nz && (f < 5 || p.has_gp)) {
-        long long n = node_id(p, i, j, k);
-        v = f < 5 ? p.fld[f][n] : p.gpf[f - 5][n];
+        const long long n = node_id(p, i, j, k);
+        cp_async(dstv, f < 5 ? p.fld[f] + n : p.gpf[f - 5] + n);
+      } else {
+        *dstv = T(0);
       }
-      sf[e] = v;
     }
+    cp_async_commit();
+    cp_async_wait<0>();
   }
   __syncthreads();
 
-  Fields<T> FG;
-  for (int f = 0; f < 5; ++f) FG.f[f] = p.fld[f];
-  for (int a = 0; a < 3; ++a) FG.g[a] = p.gpf[a];
-  const long long sxg = 1, syg = p.nx + 1, szg = (long long)(p.nx + 1) * (p.ny + 1);
+  const int ci = bi0 + lti, cj = bj0 + ltj, ck = bk0 + ltk;    // this thread's cell
+  const int cs = p.cstart[kbase + tid];
+  const int n = p.cstart[kbase + tid + 1] - cs;
+  const int nmax = __reduce_max_sync(FULL, n);
+  int off = __shfl_sync(FULL, cs, 0);            // the group's first parcel
+  T aV[8], aA[8], aB[3][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { aV[q] = 0; aA[q] = 0; aB[0][q] = 0; aB[1][q] = 0; aB[2][q] = 0; }
   T o_dp = 0, o_hn = 0, o_vs = 0;
   int kdep_lo = 1 << 30, kdep_hi = -1;          // node layers this CTA deposits into
-  const int nchunks = (pend - pstart + NC - 1) / NC;
-  if (tid == 0) issue_chunk(src, pstart, min(NC, pend - pstart), np, stage + (gk & 1) * 8 * SPAD, &mbar[gk & 1]);
 
-  for (int kc = 0; kc < nchunks; ++kc, ++gk) {
-    const int buf = (int)(gk & 1);
-    const long long c0 = (long long)pstart + (long long)kc * NC;
-    const int cn = (int)min((long long)NC, (long long)pend - c0);
-    const long long s0 = c0 & ~3LL;
-    T* sb = stage + buf * 8 * SPAD;
-    if (tid == 0 && kc + 1 < nchunks) {
-      const long long c1 = c0 + NC;
-      issue_chunk(src, c1, (int)min((long long)NC, (long long)pend - c1), np,
-                  stage + (buf ^ 1) * 8 * SPAD, &mbar[buf ^ 1]);
+  // Level r's parcel values are copied into this thread's slots of stage r % PSTAGES
+  // PSTAGES-1 levels ahead of their use; each thread reads only its own slots, so it waits
+  // only for its own copies. Every iteration commits one group (possibly empty).
+  int pf_off = off;                              // first position of the next level to prefetch
+  auto prefetch = [&](int lv) {
+    const bool a = n > lv;
+    const unsigned bl = __ballot_sync(FULL, a);
+    if (a) {
+      const long long q = pf_off + __popc(bl & below);
+      T* slot = pre + (lv % PSTAGES) * 8 * BCELLS + tid;
+#pragma unroll
+      for (int f = 0; f < 8; ++f)
+        if (MODE == 1 || f < 3 || f >= 6) cp_async(slot + f * BCELLS, src.a[f] + q);
     }
-    // one thread waits for the chunk's bulk copies; the others sleep at the barrier below
-    if (tid == 0 && !mbar_wait(&mbar[buf], (uint32_t)((gk >> 1) & 1))) {
-      atomicOr(p.errs, ERR_TIMEOUT);
-      sflag[0] = 1;
-    }
-    {  // ragged tail beyond the last full group of 4 of the arrays
-      const long long e = bulk_end(c0, cn, np);
-      const long long t0 = e > c0 ? e : c0;
-      const int ntail = (int)(c0 + cn - t0);
-      for (int t = tid; t < 8 * ntail; t += BCELLS) {
-        const int f = t / ntail;
-        const long long q = t0 + (t % ntail);
-        sb[f * SPAD + (int)(q - s0)] = src.a[f][q];
-      }
-    }
-    __syncthreads();
-    if (sflag[0]) {             // a bulk copy never completed: drain what was issued and leave
-      if (tid == 0 && kc + 1 < nchunks) mbar_wait(&mbar[buf ^ 1], (uint32_t)(((gk + 1) >> 1) & 1));
-      return;
-    }
-    // ---- phase A: one parcel per thread
-    for (int r = tid; r < cn; r += BCELLS) {
-      const long long q = c0 + r;
-      const int si = (int)(q - s0);
-      T x = sb[si], y = sb[SPAD + si], z = sb[2 * SPAD + si];
+    pf_off += __popc(bl);
+  };
+#pragma unroll
+  for (int lv = 0; lv < PSTAGES - 1; ++lv) {
+    if (lv < nmax) prefetch(lv);
+    cp_async_commit();
+  }
+  for (int r = 0; r < nmax; ++r) {
+    if (r + PSTAGES - 1 < nmax) prefetch(r + PSTAGES - 1);
+    cp_async_commit();
+    cp_async_wait<PSTAGES - 1>();
+    const bool act = n > r;
+    const unsigned bal = __ballot_sync(FULL, act);
+    if (act) {
+      const long long q = off + __popc(bal & below);
+      const T* slot = pre + (r % PSTAGES) * 8 * BCELLS + tid;
+      const T x = slot[0], y = slot[BCELLS], z = slot[2 * BCELLS];
+      const T d = slot[6 * BCELLS], om = slot[7 * BCELLS];
       Cell3<T> c;
       bin3(p, x, y, z, c);
-      const int oldcell = cell_id(p, c.i, c.j, c.k);
-      const int ti = c.i - bi0, tj = c.j - bj0, tk = c.k - bk0;
-      const bool inb = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
-      rkey[r] = inb ? ti + BX * (tj + BY * tk) : BCELLS;
+      const bool own = c.i == ci && c.j == cj && c.k == ck;
       kdep_lo = min(kdep_lo, c.k);
       kdep_hi = max(kdep_hi, c.k + 1);
+      const T V = om * (d * d * d) * p.vcoef;
       if (MODE == 0) {
-        rxn[r] = c.xi[0]; rxn[NC + r] = c.xi[1]; rxn[2 * NC + r] = c.xi[2];
-        rcn[r] = oldcell;
-        continue;
-      }
-      T u = sb[3 * SPAD + si], v = sb[4 * SPAD + si], w = sb[5 * SPAD + si];
-      T d = sb[6 * SPAD + si], om = sb[7 * SPAD + si];
-      T V = om * (d * d * d) * p.vcoef;
-      Interp<T> I;
-      if (inb)
-        interp_tile(p, sf, ti + TX * (tj + TY * tk), c.xi, I);
-      else
-        interp8(p, FG, p.has_gp != 0, node_id(p, c.i, c.j, c.k), sxg, syg, szg, c.xi, I);
-      T up[3] = {u, v, w};
-      T s[3] = {I.ug[0] - u, I.ug[1] - v, I.ug[2] - w};
-      T D = wen_yu_fast(p, d, I.es, s);
-      T f = p.rho_p * V * D;
-      o_dp += f * s[2];
-      o_hn += V * z;
-      o_vs += V;
-      rf[r] = f;
-      rxo[r] = c.xi[0]; rxo[NC + r] = c.xi[1]; rxo[2 * NC + r] = c.xi[2];
-      rco[r] = oldcell;
-      // semi-implicit push (Eq. 4 / (eps_P rho_P), drag implicit), Eq. 3, specular walls
-      T pos[3] = {x, y, z};
-      const T inv_den = frcp(T(1) + p.dt * D);
-      const T inv_esr = I.es > T(1e-12) ? frcp(I.es * p.rho_p) : T(0);
-      bool bad = false;
+        if (own) {
+          T Wq[8];
+          corner_weights(c.xi, Wq);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        T acc = D * I.ug[a] + p.g[a] - I.gp[a] * p.inv_rho_p - I.gt[a] * inv_esr;
-        T un = (up[a] + p.dt * acc) * inv_den;
-        T xn = pos[a] + p.dt * un;
-        if (xn < T(0)) { xn = -xn; un = -p.e_wall * un; }
-        else if (xn > p.L[a]) { xn = T(2) * p.L[a] - xn; un = -p.e_wall * un; }
-        if (!(xn >= T(0) && xn <= p.L[a]) || !isfinite(un)) bad = true;
-        pos[a] = xn;
-        up[a] = un;
-      }
-      if (bad) atomicOr(p.errs, ERR_DOMAIN);
-      Cell3<T> cnw;
-      bin3(p, pos[0], pos[1], pos[2], cnw);
-      const int newcell = cell_id(p, cnw.i, cnw.j, cnw.k);
-      kdep_lo = min(kdep_lo, cnw.k);
-      kdep_hi = max(kdep_hi, cnw.k + 1);
-      rxn[r] = cnw.xi[0]; rxn[NC + r] = cnw.xi[1]; rxn[2 * NC + r] = cnw.xi[2];
-      rcn[r] = newcell;
-      dst.a[0][q] = pos[0]; dst.a[1][q] = pos[1]; dst.a[2][q] = pos[2];
-      dst.a[3][q] = up[0]; dst.a[4][q] = up[1]; dst.a[5][q] = up[2];
-      if (src.a[0] != dst.a[0]) {
-        dst.a[6][q] = d; dst.a[7][q] = om;
-        if (src.pid) dst.pid[q] = src.pid[q];
-        if (src.tag) dst.tag[q] = src.tag[q];
-      }
-      if (cell_out) cell_out[q] = newcell;
-    }
-    __syncthreads();
-    // ---- grouping: records are in sorted-cell order; those whose current cell is not their
-    // sorted cell (drift since the last sort) are listed, in record order, for phase B
-    {
-      const int r0c = (int)(max((long long)p.cstart[kbase + tid], c0) - c0);
-      const int r1c = (int)(min((long long)p.cstart[kbase + tid + 1], c0 + cn) - c0);
-      cr0[tid] = r0c;
-      cr1[tid] = r1c < r0c ? r0c : r1c;
-    }
-    if (tid == 0) { sflag[2] = BCELLS; sflag[3] = -1; }
-    __syncthreads();
-    int ndrift = 0;
-    {
-      // thread t marks record t, t+256: drifted if its key is not the cell whose range holds it
-      const int seg = (NC + 7) / 8;
-      const int wlo = warp * seg, whi = min(cn, wlo + seg);
-      int wcount = 0, kmin = BCELLS, kmax = -1;
-      for (int rb = wlo; rb < whi; rb += 32) {
-        const int r = rb + lane;
-        bool dr = false;
-        if (r < whi) {
-          const int key = rkey[r];
-          dr = key == BCELLS || !(cr0[key] <= r && r < cr1[key]);
-          if (key < BCELLS) { kmin = min(kmin, key); kmax = max(kmax, key); }
-        }
-        wcount += __popc(__ballot_sync(0xffffffffu, dr));
-      }
-      kmin = __reduce_min_sync(0xffffffffu, kmin);
-      kmax = __reduce_max_sync(0xffffffffu, kmax);
-      if (lane == 0) {
-        sflag[4 + warp] = wcount;
-        atomicMin(&sflag[2], kmin);
-        atomicMax(&sflag[3], kmax);
-      }
-      __syncthreads();
-      int base = 0;
-      for (int w = 0; w < warp; ++w) base += sflag[4 + w];
-      for (int rb = wlo; rb < whi; rb += 32) {
-        const int r = rb + lane;
-        bool dr = false;
-        if (r < whi) {
-          const int key = rkey[r];
-          dr = key == BCELLS || !(cr0[key] <= r && r < cr1[key]);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, dr);
-        if (dr) drift[base + __popc(bal & lanes_below)] = r;
-        base += __popc(bal);
-      }
-      if (warp == 7 && lane == 0) sflag[1] = base;
-      __syncthreads();
-      ndrift = sflag[1];
-    }
-    // ---- phase B: G consecutive lanes per cell of [la, lb] sum its records in registers:
-    // the records of its sorted range still in it, then the drifted records now in it
-    const int la = sflag[2], lb = sflag[3];
-    const int nocc = lb >= la ? lb - la + 1 : 0;
-    int G = 1;
-    while (G < 8 && 2 * G * nocc <= BCELLS) G *= 2;
-    const int ci = tid / G, sub = tid % G;
-    T aV[8], aA[8], aB[3][8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) { aV[q] = 0; aA[q] = 0; aB[0][q] = 0; aB[1][q] = 0; aB[2][q] = 0; }
-    int l = -1;
-    if (ci < nocc) {
-      l = la + ci;
-      const int lli = l % BX, llj = (l / BX) % BY, llk = l / (BX * BY);
-      const int gcell = cell_id(p, bi0 + lli, bj0 + llj, bk0 + llk);
-      const int rs0 = cr0[l], rs1 = cr1[l];
-      const int nown = rs1 - rs0;
-      // own range first (skipping records that drifted away), then the drift list
-      for (int j = sub; j < nown + ndrift; j += G) {
-        const int r = j < nown ? rs0 + j : drift[j - nown];
-        if (rkey[r] != l) continue;
-        const int si = (int)(c0 + r - s0);
-        if (MODE == 1) {
-          const T xo[3] = {rxo[r], rxo[NC + r], rxo[2 * NC + r]};
-          const T fr = rf[r];
-          const T fu[3] = {fr * sb[3 * SPAD + si], fr * sb[4 * SPAD + si], fr * sb[5 * SPAD + si]};
-          T w[3][2];
-          for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - xo[a]; w[a][1] = xo[a]; }
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const T Wq = (w[0][q & 1] * w[1][(q >> 1) & 1]) * w[2][q >> 2];
-            aA[q] += fr * Wq;
-            aB[0][q] += fu[0] * Wq;
-            aB[1][q] += fu[1] * Wq;
-            aB[2][q] += fu[2] * Wq;
-          }
-        }
-        const T xn[3] = {rxn[r], rxn[NC + r], rxn[2 * NC + r]};
-        const T dr = sb[6 * SPAD + si];
-        const T Vr[1] = {sb[7 * SPAD + si] * (dr * dr * dr) * p.vcoef};
-        const int cnr = rcn[r];
-        if (cnr == gcell) {
-          T w[3][2];
-          for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - xn[a]; w[a][1] = xn[a]; }
-#pragma unroll
-          for (int q = 0; q < 8; ++q) aV[q] += Vr[0] * ((w[0][q & 1] * w[1][(q >> 1) & 1]) * w[2][q >> 2]);
+          for (int k = 0; k < 8; ++k) aV[k] += V * Wq[k];
         } else {
-          scatter_global<T, 1>(p, cnr, xn[0], xn[1], xn[2], Vr[0], T(0), T(0), T(0));
+          deposit_foreign<T, 1>(p, fx, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 0,
+                                V, T(0), T(0), T(0));
         }
-      }
-    }
-    // combine the G partial sums of a cell (consecutive lanes of one warp; in warps that
-    // hold an occupied cell every lane takes part)
-    const bool warp_busy = (warp * 32) / G < nocc;
-    for (int o = 1; warp_busy && o < G; o <<= 1) {
+      } else {
+        const T u = slot[3 * BCELLS], v = slot[4 * BCELLS], w = slot[5 * BCELLS];
+        const int ti = c.i - bi0, tj = c.j - bj0, tk = c.k - bk0;
+        const bool inb = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
+        Interp<T> I;
+        if (inb) {
+          interp_tile(p, sf, ti + TX * (tj + TY * tk), c.xi, I);
+        } else {  // outside the brick (rare): from the global node arrays
+          Fields<T> FG;
+          for (int f = 0; f < 5; ++f) FG.f[f] = p.fld[f];
+          for (int a = 0; a < 3; ++a) FG.g[a] = p.gpf[a];
+          interp8(p, FG, p.has_gp != 0, node_id(p, c.i, c.j, c.k), 1, p.nx + 1,
+                  (long long)(p.nx + 1) * (p.ny + 1), c.xi, I);
+        }
+        T up[3] = {u, v, w};
+        const T s[3] = {I.ug[0] - u, I.ug[1] - v, I.ug[2] - w};
+        const T D = wen_yu_fast(p, d, I.es, s);
+        const T f = p.rho_p * V * D;
+        o_dp += f * s[2];
+        o_hn += V * z;
+        o_vs += V;
+        // drag sums of the pre-push state, at the old position
+        if (own) {
+          T Wq[8];
+          corner_weights(c.xi, Wq);
+          const T fu0 = f * u, fu1 = f * v, fu2 = f * w;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        aV[q] += __shfl_xor_sync(0xffffffffu, aV[q], o);
-        if (MODE == 1) {
-          aA[q] += __shfl_xor_sync(0xffffffffu, aA[q], o);
-          aB[0][q] += __shfl_xor_sync(0xffffffffu, aB[0][q], o);
-          aB[1][q] += __shfl_xor_sync(0xffffffffu, aB[1][q], o);
-          aB[2][q] += __shfl_xor_sync(0xffffffffu, aB[2][q], o);
+          for (int k = 0; k < 8; ++k) {
+            aA[k] += f * Wq[k];
+            aB[0][k] += fu0 * Wq[k];
+            aB[1][k] += fu1 * Wq[k];
+            aB[2][k] += fu2 * Wq[k];
+          }
+        } else {
+          deposit_foreign<T, 4>(p, fx, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 1,
+                                f, f * u, f * v, f * w);
         }
-      }
-    }
-    // records whose current cell is outside the brick: straight to the global accumulators
-    for (int j = tid; j < ndrift; j += BCELLS) {
-      const int r = drift[j];
-      if (rkey[r] != BCELLS) continue;
-      const int si = (int)(c0 + r - s0);
-      if (MODE == 1) {
-        const T fr = rf[r];
-        scatter_global<T, 4>(p, rco[r], rxo[r], rxo[NC + r], rxo[2 * NC + r], fr,
-                             fr * sb[3 * SPAD + si], fr * sb[4 * SPAD + si], fr * sb[5 * SPAD + si]);
-      }
-      const T dr = sb[6 * SPAD + si];
-      scatter_global<T, 1>(p, rcn[r], rxn[r], rxn[NC + r], rxn[2 * NC + r],
-                           sb[7 * SPAD + si] * (dr * dr * dr) * p.vcoef, T(0), T(0), T(0));
-    }
-    // per-cell sums into the shared tile, one corner per phase: in a phase no two cells
-    // touch the same node, so plain adds in a fixed order are deterministic
-    const bool lead = ci < nocc && sub == 0;
-    const int tbase = lead ? (l % BX) + TX * (((l / BX) % BY) + TY * (l / (BX * BY))) : 0;
+        // semi-implicit push (Eq. 4 / (eps_P rho_P), drag implicit), Eq. 3, specular walls
+        T pos[3] = {x, y, z};
+        const T inv_den = frcp(T(1) + p.dt * D);
+        const T inv_esr = I.es > T(1e-12) ? frcp(I.es * p.rho_p) : T(0);
+        bool bad = false;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      __syncthreads();
-      if (lead) {
-        const int tn = tbase + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2));
-        tile[tn] += aV[q];
-        if (MODE == 1) {
-          tile[TNODES + tn] += aA[q];
-          tile[2 * TNODES + tn] += aB[0][q];
-          tile[3 * TNODES + tn] += aB[1][q];
-          tile[4 * TNODES + tn] += aB[2][q];
+        for (int a = 0; a < 3; ++a) {
+          const T acc = D * I.ug[a] + p.g[a] - I.gp[a] * p.inv_rho_p - I.gt[a] * inv_esr;
+          T un = (up[a] + p.dt * acc) * inv_den;
+          T xn = pos[a] + p.dt * un;
+          if (xn < T(0)) { xn = -xn; un = -p.e_wall * un; }
+          else if (xn > p.L[a]) { xn = T(2) * p.L[a] - xn; un = -p.e_wall * un; }
+          if (!(xn >= T(0) && xn <= p.L[a]) || !isfinite(un)) bad = true;
+          pos[a] = xn;
+          up[a] = un;
         }
+        if (bad) atomicOr(p.errs, ERR_DOMAIN);
+        Cell3<T> cn;
+        bin3(p, pos[0], pos[1], pos[2], cn);
+        kdep_lo = min(kdep_lo, cn.k);
+        kdep_hi = max(kdep_hi, cn.k + 1);
+        // solids volume of the new position, for the next step
+        if (cn.i == ci && cn.j == cj && cn.k == ck) {
+          T Wq[8];
+          corner_weights(cn.xi, Wq);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) aV[k] += V * Wq[k];
+        } else {
+          deposit_foreign<T, 1>(p, fx, bi0, bj0, bk0, cn.i, cn.j, cn.k, cn.xi[0], cn.xi[1],
+                                cn.xi[2], 0, V, T(0), T(0), T(0));
+        }
+        dst.a[0][q] = pos[0]; dst.a[1][q] = pos[1]; dst.a[2][q] = pos[2];
+        dst.a[3][q] = up[0]; dst.a[4][q] = up[1]; dst.a[5][q] = up[2];
+        if (copy_ro) {
+          dst.a[6][q] = d; dst.a[7][q] = om;
+          if (src.pid) dst.pid[q] = src.pid[q];
+          if (src.tag) dst.tag[q] = src.tag[q];
+        }
+        if (cell_out) cell_out[q] = cell_id(p, cn.i, cn.j, cn.k);
       }
     }
-    __syncthreads();
+    off += __popc(bal);
   }
   // ---- node layers touched by this CTA's deposits, for the next finalize
-  kdep_lo = __reduce_min_sync(0xffffffffu, kdep_lo);
-  kdep_hi = __reduce_max_sync(0xffffffffu, kdep_hi);
+  kdep_lo = __reduce_min_sync(FULL, kdep_lo);
+  kdep_hi = __reduce_max_sync(FULL, kdep_hi);
   if (lane == 0 && kdep_hi >= 0) { atomicMin(&p.zr[0], kdep_lo); atomicMax(&p.zr[1], kdep_hi); }
-  // ---- the tile, in exact fixed point, to the global accumulators
-  const int nq = MODE == 1 ? NQ : 1;
-  for (int e = tid; e < nq * TNODES; e += BCELLS) {
-    int q = e / TNODES, tn = e % TNODES;
-    int ti = tn % TX, tj = (tn / TX) % TY, tk = tn / (TX * TY);
-    int i = bi0 + ti, j = bj0 + tj, k = bk0 + tk;
-    if (i > p.nx || j > p.ny || k > p.nz) continue;
-    T v = tile[e];
-    if (v == T(0)) continue;
-    u64 fx[W];
-    to_fixed(v, q == 0 ? p.mV : p.mA, fx, p.errs);
-    acc_add(p.acc + (long long)(q * W) * p.nstride + p.nbase + node_id(p, i, j, k), p.nstride, fx);
-  }
-  if (MODE == 1) {
+  // ---- this cell's sums into the tile, one corner per phase: in a phase no two cells touch
+  // the same node, so plain adds in a fixed order are deterministic
+  const int tn0 = lti + TX * (ltj + TY * ltk);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
     __syncthreads();
-    block_sum3(o_dp, o_hn, o_vs, reinterpret_cast<T*>(smem + S::rec), obj_part + 3 * b);
+    if (n > 0) {
+      const int tn = tn0 + (k & 1) + TX * (((k >> 1) & 1) + TY * (k >> 2));
+      tile[tn] += aV[k];
+      if (MODE == 1) {
+        tile[TNODES + tn] += aA[k];
+        tile[2 * TNODES + tn] += aB[0][k];
+        tile[3 * TNODES + tn] += aB[1][k];
+        tile[4 * TNODES + tn] += aB[2][k];
+      }
+    }
   }
+  __syncthreads();
+  // ---- the tile in exact fixed point, plus the off-cell contributions, to the global
+  // accumulators
+  for (int e = tid; e < nq * TNODES; e += BCELLS) {
+    const int qq = e / TNODES, tn = e % TNODES;
+    const int i = bi0 + tn % TX, j = bj0 + (tn / TX) % TY, k = bk0 + tn / (TX * TY);
+    if (i > p.nx || j > p.ny || k > p.nz) continue;
+    u64 f[W];
+    to_fixed(tile[e], qq == 0 ? p.mV : p.mA, f, p.errs);
+    u64 carry = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const u64 g = fx[(qq * W + w) * TNODES + tn];
+      const u64 s0 = f[w] + g;
+      const u64 c1 = s0 < g ? 1ull : 0ull;
+      f[w] = s0 + carry;
+      carry = c1 + (f[w] < s0 ? 1ull : 0ull);
+    }
+    acc_add(p.acc + (long long)(qq * W) * p.nstride + p.nbase + node_id(p, i, j, k), p.nstride, f);
+  }
+  if (MODE == 1) block_sum3(o_dp, o_hn, o_vs, red, obj_part + 3 * b);
   }  // persistent loop
 }
 

@@ -162,11 +162,18 @@ def dense_bed(n=32_000_000, nx=128, ny=128, nz=512, seed=SEED_BASE + 3, eps_s=0.
     return Bed(p, parcels, nsteps=nsteps, meta=dict(workload=f"dense_{nx}x{ny}x{nz}"))
 
 
-def grad_bed(n=500_000, nx=32, ny=32, nz=128, seed=SEED_BASE + 5, nsteps=200) -> Bed:
-    """Differentiation bed: d = 150 um, 2500 kg/m3, w = 10, lower-half fill, inflow 0.4 m/s."""
+def grad_bed(n=500_000, nx=32, ny=32, nz=128, seed=SEED_BASE + 5, nsteps=200,
+             floor_clearance=0.0) -> Bed:
+    """Differentiation bed: d = 150 um, 2500 kg/m3, w = 10, lower-half fill, inflow 0.4 m/s.
+
+    floor_clearance > 0 maps the fill's z range [0, Lz/2] affinely onto
+    [floor_clearance, Lz/2] (same draws), so that no parcel reaches the floor early on."""
     rng = np.random.default_rng(seed)
     p = make_params(nx, ny, nz, u_in=0.4)
     x, y, z = _uniform_positions(rng, n, p, 0.0, 0.5)
+    if floor_clearance > 0.0:
+        half = 0.5 * nz * p["dz"]
+        z = floor_clearance + z * (half - floor_clearance) / half
     zeros = np.zeros(n)
     parcels = dict(x=x, y=y, z=z, u=zeros.copy(), v=zeros.copy(), w=zeros.copy(),
                    d=np.full(n, 150e-6), omega=np.full(n, 10.0))

@@ -89,7 +89,10 @@ def test_binning_bit_exact_including_faces(prec):
 
 
 @pytest.mark.parametrize("prec", [32, 64])
-def test_sort_is_a_stable_brick_major_permutation(prec):
+def test_sort_is_a_stable_level_permutation(prec):
+    """After a sort, the parcels of each group of 32 brick-major keys (32 cells of a brick)
+    are stored level by level: the r-th parcel of every cell of the group that has one, in
+    cell order, then level r+1; within a cell parcels keep their original order."""
     bed = synth.settle_bed(n=50_000, nx=20, ny=12, nz=9)   # grid not a multiple of the brick
     b = mppic.Bed(bed.params, precision=prec)
     dev = mppic.parcels_to_device(bed.parcels, prec, with_pid=True)
@@ -102,9 +105,15 @@ def test_sort_is_a_stable_brick_major_permutation(prec):
     i, j, k = cell % 20, (cell // 20) % 12, cell // 240
     nbx, nby = 3, 2
     key = ((i // 8) + nbx * ((j // 8) + nby * (k // 4))) * 256 + (i % 8) + 8 * ((j % 8) + 8 * (k % 4))
-    assert np.all(np.diff(key) >= 0)
-    same = np.diff(key) == 0
-    assert np.all(np.diff(pid)[same] > 0)                          # stable
+    # rank of each parcel within its key, in original order (a stable sort keeps that order)
+    order = np.lexsort((pid, key))
+    first = np.searchsorted(key[order], key[order], side="left")
+    rank = np.empty_like(pid)
+    rank[order] = np.arange(bed.np) - first
+    t = np.stack([key // 32, rank, key], axis=1)
+    d = np.diff(t, axis=0)
+    lexi_increasing = (d[:, 0] > 0) | ((d[:, 0] == 0) & ((d[:, 1] > 0) | ((d[:, 1] == 0) & (d[:, 2] > 0))))
+    assert np.all(lexi_increasing)
 
 
 # --------------------------------------------------------------- deposit --
