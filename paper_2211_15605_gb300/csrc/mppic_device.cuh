@@ -529,23 +529,6 @@ __device__ __forceinline__ T wen_yu_fast(const KParams<T>& p, T d, T es, const T
   return p.kD2 * smag * e165 * inv_de;
 }
 
-// Deterministic block reduction of three per-thread values in T, in thread order.
-template <class T>
-__device__ void block_sum3(T a, T b, T c, T* sm, double* out) {
-  const int t = threadIdx.x;
-  sm[t] = a; sm[BCELLS + t] = b; sm[2 * BCELLS + t] = c;
-  __syncthreads();
-  for (int off = BCELLS / 2; off > 0; off >>= 1) {
-    if (t < off) {
-      sm[t] += sm[t + off];
-      sm[BCELLS + t] += sm[BCELLS + t + off];
-      sm[2 * BCELLS + t] += sm[2 * BCELLS + t + off];
-    }
-    __syncthreads();
-  }
-  if (t == 0) { out[0] = (double)sm[0]; out[1] = (double)sm[BCELLS]; out[2] = (double)sm[2 * BCELLS]; }
-}
-
 // The brick's node-field tile is stored as planes of 16-byte vectors: plane k holds fields
 // VW*k .. VW*k+VW-1 of every node (VW = 4 floats or 2 doubles), node-major, so the 8
 // lanes of a quarter-warp (8 consecutive nodes along x) read 128 contiguous bytes.
@@ -565,50 +548,6 @@ __device__ __forceinline__ void tile_node(const double* t, int n, double (&v)[8]
     const double2 a = *reinterpret_cast<const double2*>(t + 2 * (k * TNODES + n));
     v[2 * k] = a.x; v[2 * k + 1] = a.y;
   }
-}
-
-// Interpolation at one parcel from the brick's node-field tile (corner (0,0,0) at tile node
-// base). The gradient of the trilinear interpolant of tau is formed from differences across
-// the cell faces: d/dx = (1/dx) sum_{b,c} (tau_1bc - tau_0bc) w_y,b w_z,c, and likewise.
-template <class T>
-__device__ __forceinline__ void interp_tile(const KParams<T>& p, const T* t, int base,
-                                            const T (&xi)[3], Interp<T>& r) {
-  T w[3][2];
-  for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - xi[a]; w[a][1] = xi[a]; }
-  T tau[8];
-  r.es = 0;
-  for (int a = 0; a < 3; ++a) { r.ug[a] = 0; r.gp[a] = 0; }
-  const bool gpf = p.has_gp != 0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
-    T v[8];
-    tile_node(t, base + a + TX * (b + TY * c), v);
-    const T W = (w[0][a] * w[1][b]) * w[2][c];
-    r.es += W * v[0];
-    r.ug[0] += W * v[1];
-    r.ug[1] += W * v[2];
-    r.ug[2] += W * v[3];
-    tau[q] = v[4];
-    if (gpf) {
-      r.gp[0] += W * v[5];
-      r.gp[1] += W * v[6];
-      r.gp[2] += W * v[7];
-    }
-  }
-  if (!gpf) { r.gp[0] = p.gp[0]; r.gp[1] = p.gp[1]; r.gp[2] = p.gp[2]; }
-  T gx = 0, gy = 0, gz = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int u0 = q & 1, u1 = q >> 1;
-    // x-faces: corners (0,u0,u1) and (1,u0,u1); y-faces: (u0,0,u1), (u0,1,u1); z: (u0,u1,0), (u0,u1,1)
-    gx += (tau[1 + 2 * u0 + 4 * u1] - tau[2 * u0 + 4 * u1]) * (w[1][u0] * w[2][u1]);
-    gy += (tau[u0 + 2 + 4 * u1] - tau[u0 + 4 * u1]) * (w[0][u0] * w[2][u1]);
-    gz += (tau[u0 + 2 * u1 + 4] - tau[u0 + 2 * u1]) * (w[0][u0] * w[1][u1]);
-  }
-  r.gt[0] = gx * p.invh[0];
-  r.gt[1] = gy * p.invh[1];
-  r.gt[2] = gz * p.invh[2];
 }
 
 // ------------------------------------------------------------ cell kernel --
@@ -647,14 +586,16 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // global accumulators. Integer additions commute, so the order of these calls does not
 // change any sum. Used for parcels that are not in their sorted cell.
 template <class T, int NV>
-__device__ __noinline__ void deposit_foreign(const KParams<T>& p, u64* fx, int i0, int j0, int k0,
-                                             int i, int j, int k, T x0, T x1, T x2, int q0,
+__device__ __noinline__ void deposit_foreign(const KParams<T>& p, u64* fx, int* kr, int i0, int j0,
+                                             int k0, int i, int j, int k, T x0, T x1, T x2, int q0,
                                              T v0, T v1, T v2, T v3) {
   constexpr int W = Words<T>::n;
   const T vals[4] = {v0, v1, v2, v3};
   const T w[3][2] = {{T(1) - x0, x0}, {T(1) - x1, x1}, {T(1) - x2, x2}};
   const int ti = i - i0, tj = j - j0, tk = k - k0;
   const bool in = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
+  atomicMin(kr, k);                              // node layers deposited into (shared)
+  atomicMax(kr + 1, k + 1);
   for (int q = 0; q < 8; ++q) {
     const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
     const T Wq = (w[0][a] * w[1][b]) * w[2][c];
@@ -672,12 +613,115 @@ __device__ __noinline__ void deposit_foreign(const KParams<T>& p, u64* fx, int i
   }
 }
 
-// Trilinear corner weights of in-cell coordinates xi, corner q = a + 2b + 4c.
+// Trilinear weights of in-cell coordinates xi: corner weights W[a + 2b + 4c], the y-z
+// products yz[b + 2c] they are built from (also the weights of d/dx of the interpolant),
+// and xi itself (the other two gradient weights are formed where they are used).
 template <class T>
-__device__ __forceinline__ void corner_weights(const T (&xi)[3], T (&Wq)[8]) {
-  const T w[3][2] = {{T(1) - xi[0], xi[0]}, {T(1) - xi[1], xi[1]}, {T(1) - xi[2], xi[2]}};
+struct Weights {
+  T W[8], yz[4], xi[3];
+};
+
+template <class T>
+__device__ __forceinline__ void corner_weights(const T (&xi)[3], T (&W)[8]) {
+  const T w0[2] = {T(1) - xi[0], xi[0]}, w1[2] = {T(1) - xi[1], xi[1]}, w2[2] = {T(1) - xi[2], xi[2]};
+  T yz[4];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) Wq[q] = (w[0][q & 1] * w[1][(q >> 1) & 1]) * w[2][q >> 2];
+  for (int q = 0; q < 4; ++q) yz[q] = w1[q & 1] * w2[q >> 1];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) W[q] = w0[q & 1] * yz[q >> 1];
+}
+
+template <class T>
+__device__ __forceinline__ void all_weights(const T (&xi)[3], Weights<T>& r) {
+  const T w0[2] = {T(1) - xi[0], xi[0]}, w1[2] = {T(1) - xi[1], xi[1]}, w2[2] = {T(1) - xi[2], xi[2]};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) r.yz[q] = w1[q & 1] * w2[q >> 1];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) r.W[q] = w0[q & 1] * r.yz[q >> 1];
+  r.xi[0] = xi[0]; r.xi[1] = xi[1]; r.xi[2] = xi[2];
+}
+
+// Interpolation at one parcel from the brick's node-field tile (corner (0,0,0) at tile node
+// base) with precomputed weights. The gradient of the trilinear interpolant of tau is
+// formed from differences across the cell faces: d/dx = (1/dx) sum_{b,c} (tau_1bc -
+// tau_0bc) w_y,b w_z,c, and likewise for y and z.
+template <class T>
+__device__ __forceinline__ void interp_tile_w(const KParams<T>& p, const T* t, int base,
+                                              const Weights<T>& w, Interp<T>& r) {
+  T tau[8];
+  r.es = 0;
+  for (int a = 0; a < 3; ++a) { r.ug[a] = 0; r.gp[a] = 0; }
+  const bool gpf = p.has_gp != 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    T v[8];
+    tile_node(t, base + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2)), v);
+    r.es += w.W[q] * v[0];
+    r.ug[0] += w.W[q] * v[1];
+    r.ug[1] += w.W[q] * v[2];
+    r.ug[2] += w.W[q] * v[3];
+    tau[q] = v[4];
+    if (gpf) {
+      r.gp[0] += w.W[q] * v[5];
+      r.gp[1] += w.W[q] * v[6];
+      r.gp[2] += w.W[q] * v[7];
+    }
+  }
+  if (!gpf) { r.gp[0] = p.gp[0]; r.gp[1] = p.gp[1]; r.gp[2] = p.gp[2]; }
+  T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int u0 = q & 1, u1 = q >> 1;
+    const T wx = u0 ? w.xi[0] : T(1) - w.xi[0];
+    const T wy = u1 ? w.xi[1] : T(1) - w.xi[1];
+    const T wz = u1 ? w.xi[2] : T(1) - w.xi[2];
+    gx += (tau[1 + 2 * u0 + 4 * u1] - tau[2 * u0 + 4 * u1]) * w.yz[q];
+    gy += (tau[u0 + 2 + 4 * u1] - tau[u0 + 4 * u1]) * (wx * wz);
+    gz += (tau[u0 + 2 * u1 + 4] - tau[u0 + 2 * u1]) * (wx * wy);
+  }
+  r.gt[0] = gx * p.invh[0];
+  r.gt[1] = gy * p.invh[1];
+  r.gt[2] = gz * p.invh[2];
+}
+
+// Wen-Yu drag coefficient in the FP32 form: the two powers of the voidage share one log2.
+__device__ __forceinline__ float wen_yu_step(const KParams<float>& p, float d, float es,
+                                             const float (&s)[3]) {
+  const float eg = fmaxf(1.0f - es, p.eg_min);
+  const float de = p.sd * d;
+  const float inv_de = __fdividef(1.0f, de);
+  const float s2 = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
+  const float smag = s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f;
+  const float rem = eg * de * smag * p.kRe;
+  const float lg = __log2f(eg);
+  if (rem < 1000.0f)
+    return p.kD1 * (1.0f + 0.15f * exp2f(0.687f * __log2f(rem))) * exp2f(-2.65f * lg) *
+           (inv_de * inv_de);
+  return p.kD2 * smag * exp2f(-1.65f * lg) * inv_de;
+}
+__device__ __forceinline__ double wen_yu_step(const KParams<double>& p, double d, double es,
+                                              const double (&s)[3]) {
+  return wen_yu_fast(p, d, es, s);
+}
+
+// Deterministic sum of three per-thread values over the CTA: a fixed shuffle tree in
+// each warp, then the warp partials in warp order.
+template <class T>
+__device__ void cta_sum3(T a, T b, T c, T* sm, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(FULL, a, o);
+    b += __shfl_down_sync(FULL, b, o);
+    c += __shfl_down_sync(FULL, c, o);
+  }
+  if (lane == 0) { sm[3 * warp] = a; sm[3 * warp + 1] = b; sm[3 * warp + 2] = c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T A = 0, B = 0, C = 0;
+    for (int w = 0; w < BCELLS / 32; ++w) { A += sm[3 * w]; B += sm[3 * w + 1]; C += sm[3 * w + 2]; }
+    out[0] = (double)A; out[1] = (double)B; out[2] = (double)C;
+  }
 }
 
 // The cell kernel. One CTA owns one brick (taken from a work counter: persistent grid);
@@ -690,12 +734,13 @@ __device__ __forceinline__ void corner_weights(const T (&xi)[3], T (&Wq)[8]) {
 // for the next step. src/dst may be the same arrays; if not, the read-only arrays are
 // copied too.
 // A thread sums the contributions of its own cell's parcels (old position for the drag
-// sums, new position for the volume) at the cell's 8 corners in registers: 40 sums,
-// converted once per brick to exact fixed point and added to a shared node tile. A
-// parcel that is not in its sorted cell (it drifted since the last sort, or moved this
-// step) adds its contributions in fixed point straight to the shared tile (or, outside
-// the brick, to the global accumulators). The tile is flushed to the global accumulators
-// once per brick. No step waits on another thread except at the brick's start and end.
+// sums, new position for the volume) at the cell's 8 corners in registers: 40 sums, added
+// once per brick to a shared node tile in 8 corner phases (no two cells of a phase share a
+// node). A parcel that is not in its sorted cell (it drifted since the last sort, or
+// moved this step) adds its contributions in exact fixed point to a second shared tile
+// (or, outside the brick, to the global accumulators). Both tiles go to the global
+// accumulators in fixed point once per brick. Threads wait on each other only at the
+// brick's start and end.
 template <class T> struct CellOccupancy;
 template <> struct CellOccupancy<float> { static constexpr int ctas = 2; };
 template <> struct CellOccupancy<double> { static constexpr int ctas = 1; };
@@ -707,9 +752,11 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         PArrays<T> dst, int* __restrict__ cell_out, double* __restrict__ obj_part, long long np) {
   typedef CellSmem<T> S;
   constexpr int W = S::W;
+  constexpr int VW = TileVec<T>::n;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ KParams<T> sp;                        // parameters of the current brick's bed
   __shared__ long long s_brick;
+  __shared__ int s_kr[2];                          // node layers deposited into by this brick
   T* sf = reinterpret_cast<T*>(smem + S::fld);     // node-field tile (planes)
   T* pre = reinterpret_cast<T*>(smem + S::pre);    // [PSTAGES][8][BCELLS] prefetched parcels
   u64* fx = reinterpret_cast<u64*>(smem + S::fx);  // [NQ][W][TNODES] parcels off their sorted cell
@@ -720,9 +767,11 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   const int lane = tid & 31;
   const unsigned below = (1u << lane) - 1u;
   const int lti = tid % BX, ltj = (tid / BX) % BY, ltk = tid / (BX * BY);
+  const int tn0 = lti + TX * (ltj + TY * ltk);   // tile node of this cell's corner (0,0,0)
   const KParams<T>& p = sp;
   int cur_bed = -1;
   const bool copy_ro = src.a[0] != dst.a[0];
+  const int nq = MODE == 1 ? NQ : 1;
 
   for (long long iter = 0; iter < total_bricks; ++iter) {
   __syncthreads();
@@ -746,21 +795,22 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     continue;
   }
 
-  const int nq = MODE == 1 ? NQ : 1;
   for (int e = tid; e < nq * W * TNODES; e += BCELLS) fx[e] = 0;
   for (int e = tid; e < nq * TNODES; e += BCELLS) tile[e] = 0;
+  if (tid == 0) { s_kr[0] = 1 << 30; s_kr[1] = -1; }
   if (MODE == 1) {
     // asynchronous copies, all in flight at once; absent nodes and fields are zero
-    constexpr int VW = TileVec<T>::n;
-    for (int e = tid; e < 8 * TNODES; e += BCELLS) {
-      const int tn = e / 8, f = e % 8;
+    for (int tn = tid; tn < TNODES; tn += BCELLS) {
       const int i = bi0 + tn % TX, j = bj0 + (tn / TX) % TY, k = bk0 + tn / (TX * TY);
-      T* dstv = sf + VW * ((f / VW) * TNODES + tn) + f % VW;
-      if (i <= p.nx && j <= p.ny && k <= p.nz && (f < 5 || p.has_gp)) {
-        const long long n = node_id(p, i, j, k);
-        cp_async(dstv, f < 5 ? p.fld[f] + n : p.gpf[f - 5] + n);
-      } else {
-        *dstv = T(0);
+      const bool in = i <= p.nx && j <= p.ny && k <= p.nz;
+      const long long nid = in ? node_id(p, i, j, k) : 0;
+#pragma unroll
+      for (int f = 0; f < 8; ++f) {
+        T* dstv = sf + VW * ((f / VW) * TNODES + tn) + f % VW;
+        if (in && (f < 5 || p.has_gp))
+          cp_async(dstv, (f < 5 ? (const T*)p.fld[f] : p.gpf[f - 5]) + nid);
+        else
+          *dstv = T(0);
       }
     }
     cp_async_commit();
@@ -777,7 +827,6 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
 #pragma unroll
   for (int q = 0; q < 8; ++q) { aV[q] = 0; aA[q] = 0; aB[0][q] = 0; aB[1][q] = 0; aB[2][q] = 0; }
   T o_dp = 0, o_hn = 0, o_vs = 0;
-  int kdep_lo = 1 << 30, kdep_hi = -1;          // node layers this CTA deposits into
 
   // Level r's parcel values are copied into this thread's slots of stage r % PSTAGES
   // PSTAGES-1 levels ahead of their use; each thread reads only its own slots, so it waits
@@ -787,7 +836,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     const bool a = n > lv;
     const unsigned bl = __ballot_sync(FULL, a);
     if (a) {
-      const long long q = pf_off + __popc(bl & below);
+      const int q = pf_off + __popc(bl & below);
       T* slot = pre + (lv % PSTAGES) * 8 * BCELLS + tid;
 #pragma unroll
       for (int f = 0; f < 8; ++f)
@@ -807,15 +856,13 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     const bool act = n > r;
     const unsigned bal = __ballot_sync(FULL, act);
     if (act) {
-      const long long q = off + __popc(bal & below);
+      const int q = off + __popc(bal & below);
       const T* slot = pre + (r % PSTAGES) * 8 * BCELLS + tid;
       const T x = slot[0], y = slot[BCELLS], z = slot[2 * BCELLS];
       const T d = slot[6 * BCELLS], om = slot[7 * BCELLS];
       Cell3<T> c;
       bin3(p, x, y, z, c);
       const bool own = c.i == ci && c.j == cj && c.k == ck;
-      kdep_lo = min(kdep_lo, c.k);
-      kdep_hi = max(kdep_hi, c.k + 1);
       const T V = om * (d * d * d) * p.vcoef;
       if (MODE == 0) {
         if (own) {
@@ -824,16 +871,18 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
 #pragma unroll
           for (int k = 0; k < 8; ++k) aV[k] += V * Wq[k];
         } else {
-          deposit_foreign<T, 1>(p, fx, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 0,
+          deposit_foreign<T, 1>(p, fx, s_kr, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 0,
                                 V, T(0), T(0), T(0));
         }
       } else {
         const T u = slot[3 * BCELLS], v = slot[4 * BCELLS], w = slot[5 * BCELLS];
         const int ti = c.i - bi0, tj = c.j - bj0, tk = c.k - bk0;
         const bool inb = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
+        Weights<T> wt;
+        all_weights(c.xi, wt);
         Interp<T> I;
         if (inb) {
-          interp_tile(p, sf, ti + TX * (tj + TY * tk), c.xi, I);
+          interp_tile_w(p, sf, ti + TX * (tj + TY * tk), wt, I);
         } else {  // outside the brick (rare): from the global node arrays
           Fields<T> FG;
           for (int f = 0; f < 5; ++f) FG.f[f] = p.fld[f];
@@ -843,25 +892,23 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         }
         T up[3] = {u, v, w};
         const T s[3] = {I.ug[0] - u, I.ug[1] - v, I.ug[2] - w};
-        const T D = wen_yu_fast(p, d, I.es, s);
+        const T D = wen_yu_step(p, d, I.es, s);
         const T f = p.rho_p * V * D;
         o_dp += f * s[2];
         o_hn += V * z;
         o_vs += V;
         // drag sums of the pre-push state, at the old position
         if (own) {
-          T Wq[8];
-          corner_weights(c.xi, Wq);
           const T fu0 = f * u, fu1 = f * v, fu2 = f * w;
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            aA[k] += f * Wq[k];
-            aB[0][k] += fu0 * Wq[k];
-            aB[1][k] += fu1 * Wq[k];
-            aB[2][k] += fu2 * Wq[k];
+            aA[k] += f * wt.W[k];
+            aB[0][k] += fu0 * wt.W[k];
+            aB[1][k] += fu1 * wt.W[k];
+            aB[2][k] += fu2 * wt.W[k];
           }
         } else {
-          deposit_foreign<T, 4>(p, fx, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 1,
+          deposit_foreign<T, 4>(p, fx, s_kr, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 1,
                                 f, f * u, f * v, f * w);
         }
         // semi-implicit push (Eq. 4 / (eps_P rho_P), drag implicit), Eq. 3, specular walls
@@ -883,8 +930,6 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         if (bad) atomicOr(p.errs, ERR_DOMAIN);
         Cell3<T> cn;
         bin3(p, pos[0], pos[1], pos[2], cn);
-        kdep_lo = min(kdep_lo, cn.k);
-        kdep_hi = max(kdep_hi, cn.k + 1);
         // solids volume of the new position, for the next step
         if (cn.i == ci && cn.j == cj && cn.k == ck) {
           T Wq[8];
@@ -892,7 +937,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
 #pragma unroll
           for (int k = 0; k < 8; ++k) aV[k] += V * Wq[k];
         } else {
-          deposit_foreign<T, 1>(p, fx, bi0, bj0, bk0, cn.i, cn.j, cn.k, cn.xi[0], cn.xi[1],
+          deposit_foreign<T, 1>(p, fx, s_kr, bi0, bj0, bk0, cn.i, cn.j, cn.k, cn.xi[0], cn.xi[1],
                                 cn.xi[2], 0, V, T(0), T(0), T(0));
         }
         dst.a[0][q] = pos[0]; dst.a[1][q] = pos[1]; dst.a[2][q] = pos[2];
@@ -907,13 +952,15 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     }
     off += __popc(bal);
   }
-  // ---- node layers touched by this CTA's deposits, for the next finalize
-  kdep_lo = __reduce_min_sync(FULL, kdep_lo);
-  kdep_hi = __reduce_max_sync(FULL, kdep_hi);
-  if (lane == 0 && kdep_hi >= 0) { atomicMin(&p.zr[0], kdep_lo); atomicMax(&p.zr[1], kdep_hi); }
+  // ---- node layers of this brick's own-cell deposits (off-cell deposits recorded theirs
+  // as they were made); merged into the global range below, for the next finalize
+  {
+    const int klo = __reduce_min_sync(FULL, n > 0 ? ck : (1 << 30));
+    const int khi = __reduce_max_sync(FULL, n > 0 ? ck + 1 : -1);
+    if (lane == 0 && khi >= 0) { atomicMin(&s_kr[0], klo); atomicMax(&s_kr[1], khi); }
+  }
   // ---- this cell's sums into the tile, one corner per phase: in a phase no two cells touch
   // the same node, so plain adds in a fixed order are deterministic
-  const int tn0 = lti + TX * (ltj + TY * ltk);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     __syncthreads();
@@ -929,26 +976,29 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     }
   }
   __syncthreads();
+  if (tid == 0 && s_kr[1] >= 0) { atomicMin(&p.zr[0], s_kr[0]); atomicMax(&p.zr[1], s_kr[1]); }
   // ---- the tile in exact fixed point, plus the off-cell contributions, to the global
   // accumulators
-  for (int e = tid; e < nq * TNODES; e += BCELLS) {
-    const int qq = e / TNODES, tn = e % TNODES;
+  for (int tn = tid; tn < TNODES; tn += BCELLS) {
     const int i = bi0 + tn % TX, j = bj0 + (tn / TX) % TY, k = bk0 + tn / (TX * TY);
     if (i > p.nx || j > p.ny || k > p.nz) continue;
-    u64 f[W];
-    to_fixed(tile[e], qq == 0 ? p.mV : p.mA, f, p.errs);
-    u64 carry = 0;
+    const long long gn = p.nbase + node_id(p, i, j, k);
+    for (int qq = 0; qq < nq; ++qq) {
+      u64 f[W];
+      to_fixed(tile[qq * TNODES + tn], qq == 0 ? p.mV : p.mA, f, p.errs);
+      u64 carry = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      const u64 g = fx[(qq * W + w) * TNODES + tn];
-      const u64 s0 = f[w] + g;
-      const u64 c1 = s0 < g ? 1ull : 0ull;
-      f[w] = s0 + carry;
-      carry = c1 + (f[w] < s0 ? 1ull : 0ull);
+      for (int w = 0; w < W; ++w) {
+        const u64 g = fx[(qq * W + w) * TNODES + tn];
+        const u64 s0 = f[w] + g;
+        const u64 c1 = s0 < g ? 1ull : 0ull;
+        f[w] = s0 + carry;
+        carry = c1 + (f[w] < s0 ? 1ull : 0ull);
+      }
+      acc_add(p.acc + (long long)(qq * W) * p.nstride + gn, p.nstride, f);
     }
-    acc_add(p.acc + (long long)(qq * W) * p.nstride + p.nbase + node_id(p, i, j, k), p.nstride, f);
   }
-  if (MODE == 1) block_sum3(o_dp, o_hn, o_vs, red, obj_part + 3 * b);
+  if (MODE == 1) cta_sum3(o_dp, o_hn, o_vs, red, obj_part + 3 * b);
   }  // persistent loop
 }
 
