@@ -13,7 +13,8 @@ Prints one JSON line. `value` is whole-job parcel-updates/s with inputs resident
 metric through the C ABI with the parcel state copied from pinned host memory before and
 back after every step. `roofline` is the fused step kernel's algorithmic bytes per launch
 over its event-timed duration against the measured HBM copy bandwidth. `cpu_baseline` is
-the FP64 CPU oracle on a bounded sample of the same bed.
+the FP64 CPU oracle on a bounded sample of the same bed. `sort_every_step` times the same bed
+sorted by cell every step (the other schedule of this workload); `fp64_form` the FP64 form.
 
 --impl reference times the oracle itself (the slow program this build is checked
 against) on a bounded sample per step, with the same metric.
@@ -52,6 +53,8 @@ def parse():
     ap.add_argument("--precision", type=int, choices=(32, 64), default=32)
     ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64-form comparison (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--sort1-steps", type=int, default=5,
+                    help="steps of the sort-every-step measurement (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="parcels in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -146,6 +149,24 @@ def measured_peak():
 
 # --------------------------------------------------------------- GPU arm --
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32 step kernel per
+# parcel, from one ncu capture on the 128x128x128 / 8M-parcel dense bed
+# (profiles/k_cells_float_dense_8M.md); the dense bed's traffic grows in proportion to its
+# parcels. Reported only while the kernel source is the one captured.
+STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 66.5,
+                "source_sha256": "09527a1810bb31a617ce3512e1c83b4d502e5e6da907fe463e8275009e5ed6c6"}
+
+
+def step_traffic(args, np_):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2211_15605_gb300", "csrc", "mppic_device.cuh")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    t = STEP_TRAFFIC
+    if args.workload != t["workload"] or args.precision != t["precision"] or sha != t["source_sha256"]:
+        return None
+    return int(round(t["bytes_per_parcel"] * np_))
+
 def bytes_per_launch(np_, active_bricks, precision):
     """Algorithmic DRAM bytes of one fused step launch: every parcel's state read once
     (x,y,z,u,v,w,d,w: 8 values) and written once (x,y,z,u,v,w: 6 values), plus per occupied
@@ -184,7 +205,7 @@ def run_gpu(args):
     parcels = mppic.parcels_to_device(bed.parcels, args.precision, device=dev)
     gas = mppic.gas_to_device(bed.U, None, args.precision, device=dev)
     nsteps_all = args.warmup + args.steps
-    obj = torch.zeros((max(nsteps_all, 1), 2), dtype=torch.float64, device=dev)
+    obj = torch.zeros((max(nsteps_all, args.sort1_steps, 2), 2), dtype=torch.float64, device=dev)
 
     # warm-up steps, then exactly --steps timed steps in one call
     if args.warmup:
@@ -218,11 +239,36 @@ def run_gpu(args):
     achieved = bpl / (step_ms / 1e3) / 1e9
     shares = {k: round(v / max(sum(prof["ms"].values()), 1e-9), 4) for k, v in prof["ms"].items()}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": step_traffic(args, bed.np),
                 "kernel": "k_cells<float,1> (fused interp/drag/push/deposit)" if args.precision == 32
                 else "k_cells<double,1>", "peak_kind": peak_kind + " (hbm_gbs copy burst)",
                 "bytes_per_launch": bpl, "ms_per_launch": round(step_ms, 5), "phase_ms": prof["ms"],
                 "phase_share": shares}
+
+    # the same bed sorted by cell every step (the other sort schedule of this workload)
+    sort1 = None
+    if args.sort1_steps > 0 and args.sort_every != 1:
+        b.tune(0, 1)
+        b.step(parcels, gas, 2, obj[:2])
+        barrier()
+        b.profile(True)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        b.step(parcels, gas, args.sort1_steps, obj[: args.sort1_steps])
+        h1.record(stream)
+        barrier()
+        pr1 = b.profile_read()
+        b.profile(False)
+        b.check()
+        sms = h0.elapsed_time(h1)
+        t1 = torch.tensor([sms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t1, op=dist.ReduceOp.MAX)
+        sort1 = {"value": world * bed.np * args.sort1_steps / (float(t1.item()) / 1e3), "unit": UNIT,
+                 "ms_per_step": float(t1.item()) / args.sort1_steps, "steps": args.sort1_steps,
+                 "sort_every": 1, "phase_ms_per_step": {k: round(v / args.sort1_steps, 4)
+                                                        for k, v in pr1["ms"].items()}}
+        b.tune(0, args.sort_every)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -291,7 +337,8 @@ def run_gpu(args):
                 "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
                 "config": workload_config(bed, args), "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": prof["total_launches"], "clocks": clk,
-                "fp64_form": fp64, "parallelism": "replicas" if world > 1 else "single"}
+                "fp64_form": fp64, "sort_every_step": sort1,
+                "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(line))
     b.close()
     if world > 1:

@@ -46,7 +46,8 @@ typedef enum {
   MPPIC_ERR_CUDA = 2,     /* a CUDA runtime call failed */
   MPPIC_ERR_OOM = 3,      /* device allocation failed */
   MPPIC_ERR_DOMAIN = 4,   /* a parcel left the box after reflection, or a value became non-finite */
-  MPPIC_ERR_TIMEOUT = 5,  /* a bounded device loop gave up */
+  MPPIC_ERR_TIMEOUT = 5,  /* a bounded device wait gave up (reserved: the current kernels
+                             have no spin-waits) */
   MPPIC_ERR_RANGE = 6     /* a fixed-point node accumulator exceeded its range */
 } mppic_status;
 
@@ -114,8 +115,12 @@ mppic_status mppic_create(const mppic_config *cfg, int nbeds, const long long *b
 
 /* Step a1-a3 (binning; optional sort by cell). Writes parcels->cell from the positions
  * with the exact FP64 formula i = clamp(floor(fl64(x * fl64(1/dx))), 0, nx-1).
- * If do_sort != 0, stably sorts all parcel arrays by a brick-major cell key (bricks of
- * 8x8x4 cells; within a brick, by cell) and records the cell ranges in the handle. */
+ * If do_sort != 0, sorts all parcel arrays by cell and records the cell ranges in the
+ * handle. The order: cells are grouped in bricks of 8x8x4 (brick-major), each brick in four
+ * groups of 32 cells (local cell index i + 8 (j + 8 k), 32 per group); within a group the
+ * parcels are stored by level: the r-th parcel of every cell of the group that has more
+ * than r parcels, in cell order, then level r + 1. Within a cell parcels keep their
+ * previous relative order (stable). parcels->cell is in the new order. */
 mppic_status mppic_bin(mppic_handle *h, mppic_parcels *parcels, int do_sort);
 
 /* Steps a4-a5: deposit the solids volume of every parcel (V = w pi (s_d d)^3 / 6, trilinear

@@ -53,6 +53,8 @@ struct mppic_handle {
   int* cstart = nullptr;     // nkeys + 1
   double* obj_part = nullptr;  // 3 x nbricks
   double* obj_tmp = nullptr;   // 2 doubles (objectives when the caller passes none)
+  double* obj_slices = nullptr;  // 3 x OBJ_BLOCKS slice partials of the objective reduction
+  unsigned* obj_count = nullptr; // blocks of the objective reduction done (reset by the last)
   int* errs = nullptr;
   int* zr = nullptr;           // node-layer ranges of deposits (see k_finalize)
   // parcel-sized scratch
@@ -332,7 +334,8 @@ mppic_status ensure_capacity(mppic_handle* h, long long np, bool want_pid) {
 // Sort the parcels currently in `cur` by brick-major cell key into the handle's sorted
 // copy, and rebuild the cell ranges. Leaves the sorted copy as the parcel source.
 template <class T>
-mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays<T> cur) {
+mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays<T> cur,
+                               bool keys_ready = false) {
   const long long np = pc->np;
   mppic_status s = ensure_capacity(h, np, pc->pid != nullptr);
   if (s) return s;
@@ -343,13 +346,14 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
   cudaStream_t st = h->stream;
   Phase ph(h, PH_SORT);
   if (np > 0) {
-    if (beds)
-      k_keys_b<T><<<blocks(np, 256), 256, 0, st>>>(beds, h->d_poff, h->nbeds, cur.a[0], cur.a[1],
-                                                    cur.a[2], h->keys[0], h->vals[0], np);
-    else
-      k_keys<T><<<blocks(np, 256), 256, 0, st>>>(p, cur.a[0], cur.a[1], cur.a[2], h->keys[0],
-                                                  h->vals[0], np);
-    LAUNCHED();
+    if (!keys_ready) {          // else the last step kernel wrote them into keys[0]
+      if (beds)
+        k_keys_b<T><<<blocks(np, 256), 256, 0, st>>>(beds, h->d_poff, h->nbeds, cur.a[0],
+                                                      cur.a[1], cur.a[2], h->keys[0], np);
+      else
+        k_keys<T><<<blocks(np, 256), 256, 0, st>>>(p, cur.a[0], cur.a[1], cur.a[2], h->keys[0], np);
+      LAUNCHED();
+    }
     const int nblk = (int)((np + SORT_TILE - 1) / SORT_TILE);
     const int passes = (h->key_bits + 7) / 8;
     int src = 0;
@@ -357,7 +361,8 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
       const int shift = 8 * ps;
       k_sort_hist<<<nblk, SORT_THREADS, 0, st>>>(h->keys[src], np, shift, h->hist, nblk);
       k_sort_scan<<<256, 1024, 0, st>>>(h->hist, nblk, h->totals);
-      k_sort_scatter<<<nblk, SORT_THREADS, 0, st>>>(h->keys[src], h->vals[src], h->keys[1 - src],
+      k_sort_scatter<<<nblk, SORT_THREADS, 0, st>>>(h->keys[src], ps ? h->vals[src] : nullptr,
+                                                     h->keys[1 - src],
                                                      h->vals[1 - src], np, shift, h->hist,
                                                      h->totals, nblk);
       LAUNCHED();
@@ -374,7 +379,7 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
     LAUNCHED();
     k_gather<T><<<blocks(np, 256), 256, 0, st>>>(
         cur, sorted_arrays<T>(h, cur.pid != nullptr, cur.tag != nullptr), h->vals[1 - src], np);
-    ph.launched(4);
+    ph.launched(keys_ready ? 3 : 4);
   } else {
     CU(cudaMemsetAsync(h->cstart, 0, sizeof(int) * (h->nkeys + 1), st));
   }
@@ -415,7 +420,7 @@ mppic_status clear_volume_accumulator(mppic_handle* h) {
 template <class T>
 mppic_status launch_cells(mppic_handle* h, int mode, const KParams<T>& p, PArrays<T> src,
                           PArrays<T> dst, int* cell_out, long long np,
-                          const KParams<T>* beds = nullptr) {
+                          const KParams<T>* beds = nullptr, uint32_t* key_out = nullptr) {
   const size_t sm = CellSmem<T>::bytes;
   static bool attr_set[2] = {false, false};
   static int resident[2] = {0, 0};
@@ -439,11 +444,11 @@ mppic_status launch_cells(mppic_handle* h, int mode, const KParams<T>& p, PArray
   ph.launched();
   if (mode == 0)
     k_cells<T, 0><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
-                                                             h->wq, src, dst, nullptr,
+                                                             h->wq, src, dst, nullptr, nullptr,
                                                              h->obj_part, np);
   else
     k_cells<T, 1><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
-                                                             h->wq, src, dst, cell_out,
+                                                             h->wq, src, dst, cell_out, key_out,
                                                              h->obj_part, np);
   LAUNCHED();
   return MPPIC_OK;
@@ -543,7 +548,7 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   for (int it = 0; it < nsteps; ++it) {
     if (it > 0 && sort_due(h->step_counter + it)) {
-      s = sort_into_scratch<T>(h, pc, dst);
+      s = sort_into_scratch<T>(h, pc, dst, true);   // keys written by the previous step
       if (s) return s;
       src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
     }
@@ -553,8 +558,10 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
     }
     s = launch_finalize<T>(h, p, nullptr, false, beds);
     if (s) return s;
+    // the step before a sort in this call writes the sort keys of the new positions
+    uint32_t* key_out = it + 1 < nsteps && sort_due(h->step_counter + it + 1) ? h->keys[0] : nullptr;
     s = launch_cells<T>(h, 1, p, src, dst, (it == nsteps - 1 && !beds) ? pc->cell : nullptr, np,
-                        beds);
+                        beds, key_out);
     if (s) return s;
     src = dst;
     {
@@ -564,8 +571,9 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
         k_obj_reduce_b<<<h->nbeds, 256, 0, h->stream>>>(
             h->obj_part, h->d_boff, h->d_area, obj_out ? obj_out + 2LL * it * h->nbeds : h->obj_tmp);
       else
-        k_obj_reduce<<<1, 1024, 0, h->stream>>>(h->obj_part, h->nbricks, area,
-                                                obj_out ? obj_out + 2 * it : h->obj_tmp);
+        k_obj_reduce<<<OBJ_BLOCKS, OBJ_THREADS, 0, h->stream>>>(
+            h->obj_part, h->nbricks, area, h->obj_slices, h->obj_count,
+            obj_out ? obj_out + 2 * it : h->obj_tmp);
       LAUNCHED();
     }
   }
@@ -858,8 +866,11 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
       alloc((void**)&h->obj_part, sizeof(double) * 3 * (nbricks > 0 ? nbricks : 1)) &&
       alloc((void**)&h->obj_tmp, sizeof(double) * 2 * nbeds) && alloc((void**)&h->errs, sizeof(int)) &&
       alloc((void**)&h->zr, sizeof(int) * 4) && alloc((void**)&h->wq, sizeof(unsigned long long)) &&
-      alloc((void**)&h->totals, sizeof(uint32_t) * 256)) {
+      alloc((void**)&h->totals, sizeof(uint32_t) * 256) &&
+      alloc((void**)&h->obj_slices, sizeof(double) * 3 * OBJ_BLOCKS) &&
+      alloc((void**)&h->obj_count, sizeof(unsigned))) {
     cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(u64) * NQ * h->words * nnode, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->obj_count, 0, sizeof(unsigned), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->errs, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fld, 0, h->tsize * 5 * nnode, h->stream);
     // no deposit yet; the first finalize covers every layer
@@ -1054,7 +1065,7 @@ mppic_status mppic_check(mppic_handle* h) {
   int flags = 0;
   CU(cudaMemcpy(&flags, h->errs, sizeof(int), cudaMemcpyDeviceToHost));
   CU(cudaMemset(h->errs, 0, sizeof(int)));
-  if (flags & ERR_TIMEOUT) return fail(h, MPPIC_ERR_TIMEOUT, "a bulk copy wait gave up");
+  if (flags & ERR_TIMEOUT) return fail(h, MPPIC_ERR_TIMEOUT, "a bounded device wait gave up");
   if (flags & ERR_RANGE) return fail(h, MPPIC_ERR_RANGE, "a fixed-point accumulator left its range");
   if (flags & ERR_DOMAIN)
     return fail(h, MPPIC_ERR_DOMAIN, "a parcel left the box after reflection or became non-finite");
@@ -1104,6 +1115,7 @@ void mppic_destroy(mppic_handle* h) {
   if (!h) return;
   cudaFree(h->acc); cudaFree(h->fld); cudaFree(h->cstart); cudaFree(h->obj_part);
   cudaFree(h->obj_tmp); cudaFree(h->errs); cudaFree(h->zr); cudaFree(h->totals); cudaFree(h->hist);
+  cudaFree(h->obj_slices); cudaFree(h->obj_count);
   for (int i = 0; i < 2; ++i) { cudaFree(h->keys[i]); cudaFree(h->vals[i]); }
   for (int f = 0; f < 8; ++f) cudaFree(h->sorted[f]);
   cudaFree(h->sorted_pid);

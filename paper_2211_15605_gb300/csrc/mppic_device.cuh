@@ -8,16 +8,17 @@
 //
 // Layout and determinism:
 //  * Cells are grouped in bricks of 8x8x4; parcels are sorted by a brick-major key
-//    (brick id * 256 + local cell id). One CTA of 256 threads owns one brick.
-//  * Deposits are exact integer fixed point: int64 for the FP32 form, int128 (two
-//    64-bit words with carry) for the FP64 form. Integer addition is associative, so
-//    every sum is independent of thread scheduling and of how far parcels drifted
-//    since the last sort; the sorted order only makes the sums cheap.
-//  * Inside a CTA, parcels are processed parcel-per-thread (coalesced loads, node
-//    fields from a shared-memory tile), each parcel leaving a small record in shared
-//    memory; then one thread per cell sums its records in registers in sorted order,
-//    converts the 40 per-cell sums once to fixed point and adds them to a shared
-//    node tile, which is flushed to the global accumulators once per brick.
+//    (brick id * 256 + local cell id). One CTA of 256 threads owns one brick, one
+//    thread one cell, one warp a group of 32 cells. Within a group the sorted parcels
+//    are stored by level (the r-th parcel of every cell that has one, then level r+1),
+//    so a warp reads each level as one contiguous run.
+//  * A thread walks its own cell's parcels and sums their contributions at the cell's 8
+//    corners in registers (solids volume, drag sums); the sums enter a shared node tile
+//    once per brick in 8 corner phases, in a fixed order. Parcels off their sorted cell
+//    (drift since the last sort, or moved this step) add exact fixed-point contributions.
+//  * Global deposits are exact integer fixed point: int64 for the FP32 form, int128 (two
+//    64-bit words with carry) for the FP64 form. Integer addition is associative, so the
+//    global sums do not depend on thread scheduling or on the order bricks finish.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -307,17 +308,15 @@ __global__ void k_bin(KParams<T> p, const T* __restrict__ x, const T* __restrict
   cell[q] = cell_id(p, c.i, c.j, c.k);
 }
 
-// Sort keys (brick-major) and identity values.
+// Sort keys (brick-major). The first radix pass takes the parcel index as the value.
 template <class T>
 __global__ void k_keys(KParams<T> p, const T* __restrict__ x, const T* __restrict__ y,
-                       const T* __restrict__ z, uint32_t* __restrict__ key,
-                       uint32_t* __restrict__ val, long long np) {
+                       const T* __restrict__ z, uint32_t* __restrict__ key, long long np) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
   Cell3<T> c;
   bin3(p, x[q], y[q], z[q], c);
   key[q] = brick_key(p, c.i, c.j, c.k);
-  val[q] = (uint32_t)q;
 }
 
 // ------------------------------------------------------------ radix sort --
@@ -732,7 +731,8 @@ __device__ void cta_sum3(T a, T b, T c, T* sm, double* out) {
 // MODE 1: one full step (interp from a shared node-field tile, drag, drag sums,
 // objectives, push, walls, re-bin), depositing the solids volume of the new positions
 // for the next step. src/dst may be the same arrays; if not, the read-only arrays are
-// copied too.
+// copied too. key_out (nullable) receives the sort key of every new position (the step
+// before a sort, so the sort needs no key pass).
 // A thread sums the contributions of its own cell's parcels (old position for the drag
 // sums, new position for the volume) at the cell's 8 corners in registers: 40 sums, added
 // once per brick to a shared node tile in 8 corner phases (no two cells of a phase share a
@@ -749,7 +749,8 @@ template <class T, int MODE>
 __global__ void __launch_bounds__(BCELLS, CellOccupancy<T>::ctas)
 k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restrict__ brick_bed,
         long long total_bricks, unsigned long long* __restrict__ work, PArrays<T> src,
-        PArrays<T> dst, int* __restrict__ cell_out, double* __restrict__ obj_part, long long np) {
+        PArrays<T> dst, int* __restrict__ cell_out, uint32_t* __restrict__ key_out,
+        double* __restrict__ obj_part, long long np) {
   typedef CellSmem<T> S;
   constexpr int W = S::W;
   constexpr int VW = TileVec<T>::n;
@@ -948,6 +949,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
           if (src.tag) dst.tag[q] = src.tag[q];
         }
         if (cell_out) cell_out[q] = cell_id(p, cn.i, cn.j, cn.k);
+        if (key_out) key_out[q] = (uint32_t)(p.bbase * BCELLS) + brick_key(p, cn.i, cn.j, cn.k);
       }
     }
     off += __popc(bal);
@@ -1107,24 +1109,44 @@ __global__ void k_count_bricks(const int* __restrict__ cstart, long long nbricks
   if (cstart[(b + 1) * BCELLS] > cstart[b * BCELLS]) atomicAdd(count, 1ull);
 }
 
-// a10: deterministic reduction of the per-brick objective partials into (dP, H).
+// a10: deterministic reduction of the per-brick objective partials into (dP, H): OBJ_BLOCKS
+// blocks each sum a fixed slice of bricks with a fixed tree; the last block to finish sums
+// the slice partials in order. obj[0] = dP = sum f s_z / area, obj[1] = H = 2 sum V z / sum V.
+constexpr int OBJ_BLOCKS = 32, OBJ_THREADS = 256;
 __global__ void k_obj_reduce(const double* __restrict__ part, long long nb, double area,
+                             double* __restrict__ slices, unsigned* __restrict__ count,
                              double* __restrict__ obj) {
-  __shared__ double s[3][1024];
+  __shared__ double s[3][OBJ_THREADS];
+  __shared__ bool last;
   const int t = threadIdx.x;
+  const long long per = (nb + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * per, hi = lo + per < nb ? lo + per : nb;
   double a = 0, b = 0, c = 0;
-  for (long long i = t; i < nb; i += blockDim.x) {
+  for (long long i = lo + t; i < hi; i += OBJ_THREADS) {
     a += part[3 * i]; b += part[3 * i + 1]; c += part[3 * i + 2];
   }
   s[0][t] = a; s[1][t] = b; s[2][t] = c;
   __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+  for (int off = OBJ_THREADS / 2; off > 0; off >>= 1) {
     if (t < off) { s[0][t] += s[0][t + off]; s[1][t] += s[1][t + off]; s[2][t] += s[2][t + off]; }
     __syncthreads();
   }
   if (t == 0) {
-    obj[0] = s[0][0] / area;
-    obj[1] = s[2][0] > 0 ? 2.0 * s[1][0] / s[2][0] : 0.0;
+    slices[3 * blockIdx.x] = s[0][0];
+    slices[3 * blockIdx.x + 1] = s[1][0];
+    slices[3 * blockIdx.x + 2] = s[2][0];
+    __threadfence();
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && t == 0) {                          // every slice is written: sum them in order
+    __threadfence();
+    const volatile double* vs = slices;
+    double A = 0, B = 0, C = 0;
+    for (unsigned k = 0; k < gridDim.x; ++k) { A += vs[3 * k]; B += vs[3 * k + 1]; C += vs[3 * k + 2]; }
+    obj[0] = A / area;
+    obj[1] = C > 0 ? 2.0 * B / C : 0.0;
+    *count = 0;                                  // ready for the next launch
   }
 }
 
@@ -1144,15 +1166,13 @@ __device__ __forceinline__ int find_bed(const long long* __restrict__ off, int n
 template <class T>
 __global__ void k_keys_b(const KParams<T>* __restrict__ beds, const long long* __restrict__ poff,
                          int nbeds, const T* __restrict__ x, const T* __restrict__ y,
-                         const T* __restrict__ z, uint32_t* __restrict__ key,
-                         uint32_t* __restrict__ val, long long np) {
+                         const T* __restrict__ z, uint32_t* __restrict__ key, long long np) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
   const KParams<T>& p = beds[find_bed(poff, nbeds, q)];
   Cell3<T> c;
   bin3(p, x[q], y[q], z[q], c);
   key[q] = (uint32_t)(p.bbase * BCELLS) + brick_key(p, c.i, c.j, c.k);
-  val[q] = (uint32_t)q;
 }
 
 template <class T>

@@ -206,6 +206,13 @@ class Bed:
             s.gradp[a] = None if gp is None else gp.data_ptr()
         return s
 
+    def _check_obj(self, obj, nsteps):
+        nb = getattr(self, "nbeds", 1)
+        if (obj is None or obj.dtype != torch.float64 or not obj.is_cuda or not obj.is_contiguous()
+                or obj.numel() < 2 * nb * nsteps):
+            raise ValueError(f"obj must be a contiguous float64 device tensor of at least "
+                             f"{nsteps} x {nb} x 2 values")
+
     def _ok(self, st):
         if st != OK:
             raise MppicError(st, self.L.mppic_last_error(self.h).decode())
@@ -242,6 +249,7 @@ class Bed:
         if obj is None:
             obj = torch.empty((max(nsteps, 1), 2), dtype=torch.float64,
                               device=parcels["x"].device)
+        self._check_obj(obj, nsteps)
         self._ok(self.L.mppic_step(self.h, ctypes.byref(ps),
                                    ctypes.byref(gs) if gs is not None else None,
                                    int(nsteps), _ptr(obj)))
@@ -263,6 +271,7 @@ class Bed:
         arguments, relaunched afterwards). obj must be a preallocated device tensor."""
         ps = self._parcels(parcels)
         gs = self._gas(gas)
+        self._check_obj(obj, nsteps)
         self._ok(self.L.mppic_step_graph(self.h, ctypes.byref(ps),
                                          ctypes.byref(gs) if gs is not None else None,
                                          int(nsteps), _ptr(obj)))
@@ -372,6 +381,7 @@ class Batch(Bed):
         if obj is None:
             obj = torch.empty((max(nsteps, 1), self.nbeds, 2), dtype=torch.float64,
                               device=parcels["x"].device)
+        self._check_obj(obj, nsteps)
         self._ok(self.L.mppic_step(self.h, ctypes.byref(ps),
                                    ctypes.byref(gs) if gs is not None else None,
                                    int(nsteps), _ptr(obj)))
