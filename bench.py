@@ -153,8 +153,8 @@ def measured_peak():
 # parcel, from one ncu capture on the 128x128x128 / 8M-parcel dense bed
 # (profiles/k_cells_float_dense_8M.md); the dense bed's traffic grows in proportion to its
 # parcels. Reported only while the kernel source is the one captured.
-STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 66.5,
-                "source_sha256": "09527a1810bb31a617ce3512e1c83b4d502e5e6da907fe463e8275009e5ed6c6"}
+STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 66.25,
+                "source_sha256": "1f32740dcbce4636ff66f34dc3c8060e08069c43a0e15bddbe2c9fb3f2ca2819"}
 
 
 def step_traffic(args, np_):

@@ -528,24 +528,45 @@ __device__ __forceinline__ T wen_yu_fast(const KParams<T>& p, T d, T es, const T
   return p.kD2 * smag * e165 * inv_de;
 }
 
-// The brick's node-field tile is stored as planes of 16-byte vectors: plane k holds fields
-// VW*k .. VW*k+VW-1 of every node (VW = 4 floats or 2 doubles), node-major, so the 8
-// lanes of a quarter-warp (8 consecutive nodes along x) read 128 contiguous bytes.
-// Fields: eps_s, u_g[3], tau, grad p[3].
+// The brick's node-field tile, in T units (VW = values per 16-byte vector: 4 floats or 2
+// doubles), node-major planes so the 8 lanes of a quarter-warp (8 consecutive nodes along
+// x) read 128 contiguous bytes:
+//   [0, 4 TNODES)        eps_s, u_g[3] as 4/VW planes of VW-vectors;
+//   [4 TNODES, 8 TNODES) grad p[3] (and a pad) the same way, filled only for a node field;
+//   [8 TNODES, 9 TNODES) tau, one value per node.
 template <class T> struct TileVec;
 template <> struct TileVec<float> { static constexpr int n = 4; };
 template <> struct TileVec<double> { static constexpr int n = 2; };
+constexpr int TILE_VALS = 9;                     // T values per node in the tile
 
-__device__ __forceinline__ void tile_node(const float* t, int n, float (&v)[8]) {
-  const float4 a = *reinterpret_cast<const float4*>(t + 4 * n);
-  const float4 b = *reinterpret_cast<const float4*>(t + 4 * (TNODES + n));
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+// Offset (in T) of field f of tile node tn.
+template <class T>
+__device__ __forceinline__ int tile_off(int f, int tn) {
+  constexpr int VW = TileVec<T>::n;
+  if (f < 4) return VW * ((f / VW) * TNODES + tn) + f % VW;
+  if (f == 4) return 8 * TNODES + tn;
+  const int g = f - 5;
+  return 4 * TNODES + VW * ((g / VW) * TNODES + tn) + g % VW;
 }
-__device__ __forceinline__ void tile_node(const double* t, int n, double (&v)[8]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const double2 a = *reinterpret_cast<const double2*>(t + 2 * (k * TNODES + n));
-    v[2 * k] = a.x; v[2 * k + 1] = a.y;
+
+__device__ __forceinline__ void tile_node(const float* t, int n, bool gpf, float (&v)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(t + 4 * n);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = t[8 * TNODES + n];
+  if (gpf) {
+    const float4 g = *reinterpret_cast<const float4*>(t + 4 * (TNODES + n));
+    v[5] = g.x; v[6] = g.y; v[7] = g.z;
+  }
+}
+__device__ __forceinline__ void tile_node(const double* t, int n, bool gpf, double (&v)[8]) {
+  const double2 a0 = *reinterpret_cast<const double2*>(t + 2 * n);
+  const double2 a1 = *reinterpret_cast<const double2*>(t + 2 * (TNODES + n));
+  v[0] = a0.x; v[1] = a0.y; v[2] = a1.x; v[3] = a1.y;
+  v[4] = t[8 * TNODES + n];
+  if (gpf) {
+    const double2 g0 = *reinterpret_cast<const double2*>(t + 2 * (2 * TNODES + n));
+    const double2 g1 = *reinterpret_cast<const double2*>(t + 2 * (3 * TNODES + n));
+    v[5] = g0.x; v[6] = g0.y; v[7] = g1.x;
   }
 }
 
@@ -557,7 +578,7 @@ template <class T>
 struct CellSmem {
   static constexpr int W = Words<T>::n;
   static constexpr size_t fld = 0;                                         // node-field tile
-  static constexpr size_t fx = rup(fld + sizeof(T) * 8 * TNODES, 128);     // [NQ][W][TNODES] u64
+  static constexpr size_t fx = rup(fld + sizeof(T) * TILE_VALS * TNODES, 128);  // [NQ][W][TNODES] u64
   static constexpr size_t tile = rup(fx + sizeof(u64) * NQ * W * TNODES, 128);  // [NQ][TNODES] T
   static constexpr size_t red = rup(tile + sizeof(T) * NQ * TNODES, 128);  // [3][BCELLS] T
   static constexpr size_t pre = rup(red + sizeof(T) * 3 * BCELLS, 128);    // [PSTAGES][8][BCELLS] T
@@ -654,7 +675,7 @@ __device__ __forceinline__ void interp_tile_w(const KParams<T>& p, const T* t, i
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     T v[8];
-    tile_node(t, base + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2)), v);
+    tile_node(t, base + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2)), gpf, v);
     r.es += w.W[q] * v[0];
     r.ug[0] += w.W[q] * v[1];
     r.ug[1] += w.W[q] * v[2];
@@ -753,7 +774,6 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         double* __restrict__ obj_part, long long np) {
   typedef CellSmem<T> S;
   constexpr int W = S::W;
-  constexpr int VW = TileVec<T>::n;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ KParams<T> sp;                        // parameters of the current brick's bed
   __shared__ long long s_brick;
@@ -807,8 +827,9 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
       const long long nid = in ? node_id(p, i, j, k) : 0;
 #pragma unroll
       for (int f = 0; f < 8; ++f) {
-        T* dstv = sf + VW * ((f / VW) * TNODES + tn) + f % VW;
-        if (in && (f < 5 || p.has_gp))
+        if (f >= 5 && !p.has_gp) continue;       // grad p planes are read only for a node field
+        T* dstv = sf + tile_off<T>(f, tn);
+        if (in)
           cp_async(dstv, (f < 5 ? (const T*)p.fld[f] : p.gpf[f - 5]) + nid);
         else
           *dstv = T(0);
