@@ -361,24 +361,28 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
       const int shift = 8 * ps;
       k_sort_hist<<<nblk, SORT_THREADS, 0, st>>>(h->keys[src], np, shift, h->hist, nblk);
       k_sort_scan<<<256, 1024, 0, st>>>(h->hist, nblk, h->totals);
-      k_sort_scatter<<<nblk, SORT_THREADS, 0, st>>>(h->keys[src], ps ? h->vals[src] : nullptr,
-                                                     h->keys[1 - src],
-                                                     h->vals[1 - src], np, shift, h->hist,
-                                                     h->totals, nblk);
+      if (ps == 0)                // values are the parcel indices; keys spread over digits
+        k_sort_scatter_reorder<<<nblk, SORT_THREADS, 0, st>>>(h->keys[src], nullptr,
+                                                              h->keys[1 - src], h->vals[1 - src],
+                                                              np, shift, h->hist, h->totals, nblk);
+      else
+        k_sort_scatter_direct<<<nblk, SORT_THREADS, 0, st>>>(h->keys[src], h->vals[src],
+                                                             h->keys[1 - src], h->vals[1 - src],
+                                                             np, shift, h->hist, h->totals, nblk);
       LAUNCHED();
       ph.launched(3);
       src = 1 - src;
     }
-    k_cell_starts<<<blocks(h->nkeys + 1, 256), 256, 0, st>>>(h->keys[src], np, h->nkeys,
-                                                             h->cstart);
+    k_brick_starts<<<blocks(h->nbricks + 1, 256), 256, 0, st>>>(h->keys[src], np, h->nbricks,
+                                                                 h->cstart);
     LAUNCHED();
-    // level layout within each group of 32 keys, into the value buffer the last pass freed
+    k_cell_starts<<<blocks(h->nbricks * 32, 256), 256, 0, st>>>(h->keys[src], h->nbricks, h->cstart);
+    LAUNCHED();
+    // the sorted copy, in the level layout of each group of 32 keys
     const long long ngroups = h->nkeys / 32;
-    k_level_perm<<<blocks(ngroups * 32, 256), 256, 0, st>>>(h->vals[src], h->cstart, ngroups,
-                                                             h->vals[1 - src]);
-    LAUNCHED();
-    k_gather<T><<<blocks(np, 256), 256, 0, st>>>(
-        cur, sorted_arrays<T>(h, cur.pid != nullptr, cur.tag != nullptr), h->vals[1 - src], np);
+    k_level_gather<T><<<blocks(ngroups * 32, 256), 256, 0, st>>>(
+        cur, sorted_arrays<T>(h, cur.pid != nullptr, cur.tag != nullptr), h->vals[src], h->cstart,
+        ngroups);
     ph.launched(keys_ready ? 3 : 4);
   } else {
     CU(cudaMemsetAsync(h->cstart, 0, sizeof(int) * (h->nkeys + 1), st));

@@ -368,7 +368,14 @@ __global__ void k_sort_scan(uint32_t* __restrict__ hist, int nblk, uint32_t* __r
   if (threadIdx.x == blockDim.x - 1) totals[blockIdx.x] = part[threadIdx.x];
 }
 
-__global__ void k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+// Two forms of the stable scatter of one digit pass. Both rank each warp's segment with
+// __match_any_sync. k_sort_scatter_direct writes every key straight to its output
+// position: best when a tile's keys mostly share a digit (the upper digits of nearly
+// sorted keys). k_sort_scatter_reorder first places the tile in digit order in shared
+// memory and writes it out in that order, so each digit's run lands on consecutive
+// positions: best when a tile's keys spread over many digits (the lowest digit).
+__global__ void __launch_bounds__(SORT_THREADS)
+k_sort_scatter_direct(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                long long n, int shift, const uint32_t* __restrict__ hist,
                                const uint32_t* __restrict__ totals, int nblk) {
@@ -440,17 +447,139 @@ __global__ void k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t*
   }
 }
 
-// First sorted position of each key k in [0, nkeys]: lower bound in the sorted keys.
-__global__ void k_cell_starts(const uint32_t* __restrict__ skey, long long n, long long nkeys,
-                              int* __restrict__ start) {
-  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (k > nkeys) return;
+__global__ void __launch_bounds__(SORT_THREADS)
+k_sort_scatter_reorder(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, long long n, int shift,
+               const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals, int nblk) {
+  __shared__ uint32_t dbase[256];                // output start of each digit for this tile
+  __shared__ uint32_t lbase[256];                // start of each digit in the tile's digit order
+  __shared__ uint32_t wcnt[SORT_WARPS][256];
+  __shared__ uint32_t sk[SORT_TILE], sv[SORT_TILE];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long tbase = (long long)blockIdx.x * SORT_TILE;
+  const int tn = (int)(n - tbase < SORT_TILE ? n - tbase : SORT_TILE);
+  // digit base = exclusive scan of the digit totals + this tile's offset within the digit
+  {
+    __shared__ uint32_t tot[256];
+    tot[tid] = totals[tid];
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+      uint32_t t = tid >= off ? tot[tid - off] : 0u;
+      __syncthreads();
+      tot[tid] += t;
+      __syncthreads();
+    }
+    dbase[tid] = (tid ? tot[tid - 1] : 0u) + hist[(long long)tid * nblk + blockIdx.x];
+  }
+  for (int w = 0; w < SORT_WARPS; ++w) wcnt[w][tid] = 0;
+  __syncthreads();
+  const int seg = warp * SORT_SEG;
+  const unsigned lt = (1u << lane) - 1u;
+  // count this warp's segment
+  for (int c = 0; c < SORT_SEG; c += 32) {
+    const int r = seg + c + lane;
+    const bool ok = r < tn;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (!act) break;
+    if (ok) {
+      const uint32_t d = (kin[tbase + r] >> shift) & 255u;
+      const unsigned m = __match_any_sync(act, d);
+      if ((m & lt) == 0) wcnt[warp][d] += __popc(m);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: each warp's offset within the digit, and the digit's start in the tile
+  uint32_t cnt = 0;
+  {
+    uint32_t run = 0;
+    for (int w = 0; w < SORT_WARPS; ++w) {
+      const uint32_t c = wcnt[w][tid];
+      wcnt[w][tid] = run;
+      run += c;
+    }
+    cnt = run;
+  }
+  lbase[tid] = cnt;
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {      // inclusive scan of the digit counts
+    const uint32_t t = tid >= off ? lbase[tid - off] : 0u;
+    __syncthreads();
+    lbase[tid] += t;
+    __syncthreads();
+  }
+  const uint32_t incl = lbase[tid];
+  __syncthreads();
+  lbase[tid] = incl - cnt;                       // exclusive
+  __syncthreads();
+  // place the tile in digit order (stable: warp order, then chunk order, then lane order)
+  for (int c = 0; c < SORT_SEG; c += 32) {
+    const int r = seg + c + lane;
+    const bool ok = r < tn;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (!act) break;
+    uint32_t d = 0;
+    unsigned m = 0;
+    if (ok) {
+      const uint32_t k = kin[tbase + r];
+      d = (k >> shift) & 255u;
+      m = __match_any_sync(act, d);
+      const uint32_t loc = lbase[d] + wcnt[warp][d] + __popc(m & lt);
+      sk[loc] = k;
+      sv[loc] = vin ? vin[tbase + r] : (uint32_t)(tbase + r);
+    }
+    __syncwarp();
+    if (ok && (m & lt) == 0) wcnt[warp][d] += __popc(m);
+    __syncwarp();
+  }
+  __syncthreads();
+  // write out in digit order: each digit's run of the tile lands on consecutive positions
+  for (int i = tid; i < tn; i += SORT_THREADS) {
+    const uint32_t k = sk[i];
+    const uint32_t d = (k >> shift) & 255u;
+    const uint32_t pos = dbase[d] + (uint32_t)i - lbase[d];
+    kout[pos] = k;
+    vout[pos] = sv[i];
+  }
+}
+
+// First sorted position of each key k in [0, nkeys], in two levels: k_brick_starts finds
+// the first position of every brick's first key (b * 256, b in [0, nbricks]) by binary
+// search; k_cell_starts then gives each brick one warp, which walks the brick's sorted
+// keys once and writes the start of each of its 256 keys (a key with no parcels starts at
+// the next key's first parcel).
+__global__ void k_brick_starts(const uint32_t* __restrict__ skey, long long n, long long nbricks,
+                               int* __restrict__ start) {
+  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b > nbricks) return;
+  const long long k = b * BCELLS;
   long long lo = 0, hi = n;
   while (lo < hi) {
-    long long mid = (lo + hi) >> 1;
+    const long long mid = (lo + hi) >> 1;
     if ((long long)skey[mid] < k) lo = mid + 1; else hi = mid;
   }
   start[k] = (int)lo;
+}
+
+__global__ void k_cell_starts(const uint32_t* __restrict__ skey, long long nbricks,
+                              int* __restrict__ start) {
+  const long long b = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= nbricks) return;                      // whole warps leave together
+  const long long k0 = b * BCELLS;
+  const int bs = start[k0], be = start[k0 + BCELLS];
+  // keys (key[q-1], key[q]] start at q, for q in (bs, be); keys (k0, key[bs]] start at bs
+  for (int q0 = bs; q0 < be; q0 += 32) {
+    const int q = q0 + lane;
+    if (q < be) {
+      const long long k = skey[q];
+      const long long prev = q == bs ? k0 : (long long)skey[q - 1];
+      for (long long kk = prev + 1; kk <= k; ++kk) start[kk] = q;
+    }
+  }
+  // keys after the brick's last parcel (all of them if the brick is empty) start at be
+  const long long last = be > bs ? (long long)skey[be - 1] : k0;
+  for (long long kk = last + 1 + lane; kk < k0 + BCELLS; kk += 32) start[kk] = be;
 }
 
 // Permute the parcel arrays by the sorted order.
@@ -461,18 +590,6 @@ struct PArrays {
   int* tag;       // the handle's identity array while checkpointing (optional)
 };
 
-template <class T>
-__global__ void k_gather(PArrays<T> src, PArrays<T> dst, const uint32_t* __restrict__ perm,
-                         long long np) {
-  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= np) return;
-  uint32_t s = perm[q];
-#pragma unroll
-  for (int f = 0; f < 8; ++f) dst.a[f][q] = src.a[f][s];
-  if (src.pid) dst.pid[q] = src.pid[s];
-  if (src.tag) dst.tag[q] = src.tag[s];
-}
-
 // ------------------------------------------------------------ level layout --
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -481,9 +598,11 @@ constexpr unsigned FULL = 0xffffffffu;
 // (32 cells of a brick). Within each group the parcels are laid out by level: level r
 // holds the r-th parcel (in sorted order) of every cell of the group that has more than
 // r parcels, in cell order. Then the warp's r-th iteration reads one contiguous run.
-// perm_out[level position] = perm_in[cell-sorted position]; one warp per group.
-__global__ void k_level_perm(const uint32_t* __restrict__ perm_in, const int* __restrict__ start,
-                             long long ngroups, uint32_t* __restrict__ perm_out) {
+// k_level_gather permutes the parcel arrays into that layout straight from the sorted
+// order (perm: sorted position -> source index); one warp per group.
+template <class T>
+__global__ void k_level_gather(PArrays<T> src, PArrays<T> dst, const uint32_t* __restrict__ perm,
+                               const int* __restrict__ start, long long ngroups) {
   const long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (g >= ngroups) return;                      // whole warps leave together
@@ -496,7 +615,14 @@ __global__ void k_level_perm(const uint32_t* __restrict__ perm_in, const int* __
   for (int r = 0; r < nmax; ++r) {
     const bool act = n > r;
     const unsigned bal = __ballot_sync(FULL, act);
-    if (act) perm_out[off + __popc(bal & below)] = perm_in[cs + r];
+    if (act) {
+      const int q = off + __popc(bal & below);
+      const uint32_t s = perm[cs + r];
+#pragma unroll
+      for (int f = 0; f < 8; ++f) dst.a[f][q] = src.a[f][s];
+      if (src.pid) dst.pid[q] = src.pid[s];
+      if (src.tag) dst.tag[q] = src.tag[s];
+    }
     off += __popc(bal);
   }
 }
@@ -746,7 +872,7 @@ __device__ void cta_sum3(T a, T b, T c, T* sm, double* out) {
 
 // The cell kernel. One CTA owns one brick (taken from a work counter: persistent grid);
 // thread t owns local cell t, warp w the group of cells 32w..32w+31, whose parcels are
-// stored by level (k_level_perm). The warp's r-th iteration processes the r-th parcel of
+// stored by level (k_level_gather). The warp's r-th iteration processes the r-th parcel of
 // each of its cells that has one, one per thread, with coalesced loads and stores.
 // MODE 0: deposit the solids volume of the current positions.
 // MODE 1: one full step (interp from a shared node-field tile, drag, drag sums,
