@@ -51,6 +51,7 @@ struct mppic_handle {
   u64* acc = nullptr;        // [NQ][words][nnode]
   void* fld = nullptr;       // 5 x nnode T
   int* cstart = nullptr;     // nkeys + 1
+  uint8_t* cellmap = nullptr;  // nbricks * 256: cells ranked by parcel count per brick
   double* obj_part = nullptr;  // 3 x nbricks
   double* obj_tmp = nullptr;   // 2 doubles (objectives when the caller passes none)
   double* obj_slices = nullptr;  // 3 x OBJ_BLOCKS slice partials of the objective reduction
@@ -223,6 +224,7 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   p.errs = h->errs;
   p.zr = h->zr;
   p.cstart = h->cstart;
+  p.cellmap = h->cellmap;
   return p;
 }
 
@@ -241,7 +243,7 @@ mppic_status upload_beds(mppic_handle* h, const mppic_gas* gas, const KParams<T>
     tmp.nbx = (c.nx + BX - 1) / BX; tmp.nby = (c.ny + BY - 1) / BY; tmp.nbz = (c.nz + BZ - 1) / BZ;
     tmp.nnode = h->noff[b + 1] - h->noff[b];
     tmp.nbricks = h->boff[b + 1] - h->boff[b];
-    tmp.fld = h->fld; tmp.acc = h->acc; tmp.errs = h->errs; tmp.cstart = h->cstart; tmp.zr = h->zr;
+    tmp.fld = h->fld; tmp.acc = h->acc; tmp.errs = h->errs; tmp.cstart = h->cstart; tmp.cellmap = h->cellmap; tmp.zr = h->zr;
     KParams<T> p = make_params<T>(&tmp, nullptr);
     p.nbase = h->noff[b];
     p.bbase = h->boff[b];
@@ -257,7 +259,7 @@ mppic_status upload_beds(mppic_handle* h, const mppic_gas* gas, const KParams<T>
         for (int a = 0; a < 3; ++a) p.gpf[a] = static_cast<const T*>(gas->gradp[a]) + h->noff[b];
       }
     }
-    tmp.fld = nullptr; tmp.acc = nullptr; tmp.errs = nullptr; tmp.cstart = nullptr; tmp.zr = nullptr;
+    tmp.fld = nullptr; tmp.acc = nullptr; tmp.errs = nullptr; tmp.cstart = nullptr; tmp.cellmap = nullptr; tmp.zr = nullptr;
     v[b] = p;
   }
   const size_t bytes = sizeof(KParams<T>) * h->nbeds;
@@ -378,11 +380,10 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
     LAUNCHED();
     k_cell_starts<<<blocks(h->nbricks * 32, 256), 256, 0, st>>>(h->keys[src], h->nbricks, h->cstart);
     LAUNCHED();
-    // the sorted copy, in the level layout of each group of 32 keys
-    const long long ngroups = h->nkeys / 32;
-    k_level_gather<T><<<blocks(ngroups * 32, 256), 256, 0, st>>>(
+    // the sorted copy, in the level layout of each group of 32 count-ranked cells
+    k_level_gather<T><<<(unsigned)h->nbricks, BCELLS, 0, st>>>(
         cur, sorted_arrays<T>(h, cur.pid != nullptr, cur.tag != nullptr), h->vals[src], h->cstart,
-        ngroups);
+        h->cellmap);
     ph.launched(keys_ready ? 3 : 4);
   } else {
     CU(cudaMemsetAsync(h->cstart, 0, sizeof(int) * (h->nkeys + 1), st));
@@ -871,10 +872,16 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
       alloc((void**)&h->obj_tmp, sizeof(double) * 2 * nbeds) && alloc((void**)&h->errs, sizeof(int)) &&
       alloc((void**)&h->zr, sizeof(int) * 4) && alloc((void**)&h->wq, sizeof(unsigned long long)) &&
       alloc((void**)&h->totals, sizeof(uint32_t) * 256) &&
+      alloc((void**)&h->cellmap, (size_t)BCELLS * (nbricks > 0 ? nbricks : 1)) &&
       alloc((void**)&h->obj_slices, sizeof(double) * 3 * OBJ_BLOCKS) &&
       alloc((void**)&h->obj_count, sizeof(unsigned))) {
     cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(u64) * NQ * h->words * nnode, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->obj_count, 0, sizeof(unsigned), h->stream);
+    if (e == cudaSuccess) {                      // identity cell map until the first sort
+      std::vector<uint8_t> id((size_t)BCELLS * (nbricks > 0 ? nbricks : 1));
+      for (size_t i = 0; i < id.size(); ++i) id[i] = (uint8_t)(i % BCELLS);
+      e = cudaMemcpy(h->cellmap, id.data(), id.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->errs, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fld, 0, h->tsize * 5 * nnode, h->stream);
     // no deposit yet; the first finalize covers every layer
@@ -1119,7 +1126,7 @@ void mppic_destroy(mppic_handle* h) {
   if (!h) return;
   cudaFree(h->acc); cudaFree(h->fld); cudaFree(h->cstart); cudaFree(h->obj_part);
   cudaFree(h->obj_tmp); cudaFree(h->errs); cudaFree(h->zr); cudaFree(h->totals); cudaFree(h->hist);
-  cudaFree(h->obj_slices); cudaFree(h->obj_count);
+  cudaFree(h->obj_slices); cudaFree(h->obj_count); cudaFree(h->cellmap);
   for (int i = 0; i < 2; ++i) { cudaFree(h->keys[i]); cudaFree(h->vals[i]); }
   for (int f = 0; f < 8; ++f) cudaFree(h->sorted[f]);
   cudaFree(h->sorted_pid);

@@ -70,6 +70,8 @@ struct KParams {
   int* errs;
   int* zr;                   // node-layer ranges: [0,1] touched by the last deposit, [2,3] last finalized
   const int* cstart;         // [nkeys+1]: first sorted parcel of each brick-major key
+  const uint8_t* cellmap;    // [nbricks*256]: local cell of thread t of each brick (own
+                             // order, or ranked by parcel count; chosen at the last sort)
 };
 
 template <class T> struct Words;
@@ -594,24 +596,82 @@ struct PArrays {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// The step kernel runs one thread per cell, one warp per group of 32 consecutive keys
-// (32 cells of a brick). Within each group the parcels are laid out by level: level r
-// holds the r-th parcel (in sorted order) of every cell of the group that has more than
-// r parcels, in cell order. Then the warp's r-th iteration reads one contiguous run.
-// k_level_gather permutes the parcel arrays into that layout straight from the sorted
-// order (perm: sorted position -> source index); one warp per group.
+// The step kernel runs one thread per cell and one warp per group of 32 cells of a brick.
+// A warp iterates as often as its fullest cell holds parcels. Where the brick's cells hold
+// very uneven numbers (a sparse bed, or a brick cut by the domain boundary), the cells are
+// ranked by parcel count (descending, ties by cell index) and warp w takes ranks
+// 32w..32w+31, so a warp's cells hold similar numbers and empty cells share warps that
+// finish at once; otherwise thread t keeps cell t (a warp's cells then form an 8x4 block,
+// whose node-tile reads are conflict-free). The choice is made per brick at each sort:
+// ranking is taken if it saves more than a quarter of the warp iterations (it is not tried
+// where no cell is empty and the largest count is at most 1.5 times the smallest). Within a
+// group the parcels are laid out by level: level r holds the r-th parcel (in sorted order)
+// of every cell of the group that has more than r parcels, in rank order; the warp's r-th
+// iteration then reads one contiguous run.
+// k_level_gather ranks the cells (a bitonic sort in shared memory), records the mapping in
+// cellmap, and permutes the parcel arrays into the layout straight from the sorted order
+// (perm: sorted position -> source index). One CTA per brick.
 template <class T>
-__global__ void k_level_gather(PArrays<T> src, PArrays<T> dst, const uint32_t* __restrict__ perm,
-                               const int* __restrict__ start, long long ngroups) {
-  const long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (g >= ngroups) return;                      // whole warps leave together
-  const long long key = g * 32 + lane;
-  const int cs = start[key];
-  const int n = start[key + 1] - cs;
+__global__ void __launch_bounds__(BCELLS)
+k_level_gather(PArrays<T> src, PArrays<T> dst, const uint32_t* __restrict__ perm,
+               const int* __restrict__ start, uint8_t* __restrict__ cellmap) {
+  __shared__ uint32_t sk[BCELLS];
+  __shared__ int wa[BCELLS / 32], wb[BCELLS / 32];
+  __shared__ bool s_rank;
+  const long long b = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const long long k0 = b * BCELLS;
+  const int bs = start[k0], be = start[k0 + BCELLS];
+  const int cnt = start[k0 + t + 1] - start[k0 + t];
+  // even counts (no empty cell, the largest at most 1.5 x the smallest): ranking cannot
+  // save a quarter of the warp iterations, and is skipped
+  {
+    const int mn = __reduce_min_sync(FULL, cnt), mx = __reduce_max_sync(FULL, cnt);
+    if (lane == 0) { wa[warp] = mn; wb[warp] = mx; }
+    __syncthreads();
+    if (t == 0) {
+      int bmn = wa[0], bmx = wb[0];
+      for (int w = 1; w < BCELLS / 32; ++w) { bmn = min(bmn, wa[w]); bmx = max(bmx, wb[w]); }
+      s_rank = !(bmn > 0 && 2 * bmx <= 3 * bmn);
+    }
+    __syncthreads();
+  }
+  int cell = t;
+  if (s_rank) {                                  // uniform over the CTA
+    sk[t] = ((0xFFFFFFu - (uint32_t)min(cnt, 0xFFFFFF)) << 8) | (uint32_t)t;
+    __syncthreads();
+    for (int k = 2; k <= BCELLS; k <<= 1) {      // ascending bitonic sort of unique keys
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int ixj = t ^ j;
+        if (ixj > t) {
+          const uint32_t a = sk[t], c = sk[ixj];
+          if ((a > c) == ((t & k) == 0)) { sk[t] = c; sk[ixj] = a; }
+        }
+        __syncthreads();
+      }
+    }
+    // ranked only if it saves more than a quarter of the warp iterations (the sum over
+    // warps of the warp's largest count)
+    const int rc = (int)(0xFFFFFFu - (sk[t] >> 8));  // count of the cell of rank t
+    const int m_own = __reduce_max_sync(FULL, cnt), m_rank = __reduce_max_sync(FULL, rc);
+    if (lane == 0) { wa[warp] = m_own; wb[warp] = m_rank; }
+    __syncthreads();
+    int sum_own = 0, sum_rank = 0;
+    for (int w = 0; w < BCELLS / 32; ++w) { sum_own += wa[w]; sum_rank += wb[w]; }
+    if (4 * sum_rank < 3 * sum_own) cell = (int)(sk[t] & 255u);
+    __syncthreads();                             // wa is reused below
+  }
+  cellmap[k0 + t] = (uint8_t)cell;
+  if (bs == be) return;                          // the whole CTA: an empty brick
+  const int cs = start[k0 + cell];
+  const int n = start[k0 + cell + 1] - cs;
+  const int ws = __reduce_add_sync(FULL, n);
+  if (lane == 0) wa[warp] = ws;
+  __syncthreads();
+  int off = bs;                                  // first parcel of this warp's group
+  for (int w = 0; w < warp; ++w) off += wa[w];
   const int nmax = __reduce_max_sync(FULL, n);
   const unsigned below = (1u << lane) - 1u;
-  int off = __shfl_sync(FULL, cs, 0);
   for (int r = 0; r < nmax; ++r) {
     const bool act = n > r;
     const unsigned bal = __ballot_sync(FULL, act);
@@ -871,8 +931,9 @@ __device__ void cta_sum3(T a, T b, T c, T* sm, double* out) {
 }
 
 // The cell kernel. One CTA owns one brick (taken from a work counter: persistent grid);
-// thread t owns local cell t, warp w the group of cells 32w..32w+31, whose parcels are
-// stored by level (k_level_gather). The warp's r-th iteration processes the r-th parcel of
+// thread t owns the cell cellmap gives it (its own cell, or the cell of count rank t),
+// warp w the group of threads 32w..32w+31, whose parcels are stored by level
+// (k_level_gather). The warp's r-th iteration processes the r-th parcel of
 // each of its cells that has one, one per thread, with coalesced loads and stores.
 // MODE 0: deposit the solids volume of the current positions.
 // MODE 1: one full step (interp from a shared node-field tile, drag, drag sums,
@@ -910,11 +971,10 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   T* tile = reinterpret_cast<T*>(smem + S::tile);  // [NQ][TNODES] sums of the cells' own parcels
   T* red = reinterpret_cast<T*>(smem + S::red);
 
+  __shared__ int s_wsum[BCELLS / 32];             // parcels of each warp's cells
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
+  const int lane = tid & 31, warp = tid >> 5;
   const unsigned below = (1u << lane) - 1u;
-  const int lti = tid % BX, ltj = (tid / BX) % BY, ltk = tid / (BX * BY);
-  const int tn0 = lti + TX * (ltj + TY * ltk);   // tile node of this cell's corner (0,0,0)
   const KParams<T>& p = sp;
   int cur_bed = -1;
   const bool copy_ro = src.a[0] != dst.a[0];
@@ -942,6 +1002,15 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     continue;
   }
 
+  // this thread's cell (from the cell map of the last sort) and its parcels
+  const int lc = p.cellmap[kbase + tid];
+  const int lti = lc % BX, ltj = (lc / BX) % BY, ltk = lc / (BX * BY);
+  const int tn0 = lti + TX * (ltj + TY * ltk);   // tile node of this cell's corner (0,0,0)
+  const int n = p.cstart[kbase + lc + 1] - p.cstart[kbase + lc];
+  {
+    const int ws = __reduce_add_sync(FULL, n);
+    if (lane == 0) s_wsum[warp] = ws;
+  }
   for (int e = tid; e < nq * W * TNODES; e += BCELLS) fx[e] = 0;
   for (int e = tid; e < nq * TNODES; e += BCELLS) tile[e] = 0;
   if (tid == 0) { s_kr[0] = 1 << 30; s_kr[1] = -1; }
@@ -967,10 +1036,9 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   __syncthreads();
 
   const int ci = bi0 + lti, cj = bj0 + ltj, ck = bk0 + ltk;    // this thread's cell
-  const int cs = p.cstart[kbase + tid];
-  const int n = p.cstart[kbase + tid + 1] - cs;
   const int nmax = __reduce_max_sync(FULL, n);
-  int off = __shfl_sync(FULL, cs, 0);            // the group's first parcel
+  int off = p.cstart[kbase];                     // the group's first parcel
+  for (int w = 0; w < warp; ++w) off += s_wsum[w];
   T aV[8], aA[8], aB[3][8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) { aV[q] = 0; aA[q] = 0; aB[0][q] = 0; aB[1][q] = 0; aB[2][q] = 0; }
