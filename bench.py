@@ -14,7 +14,9 @@ metric through the C ABI with the parcel state copied from pinned host memory be
 back after every step. `roofline` is the fused step kernel's algorithmic bytes per launch
 over its event-timed duration against the measured HBM copy bandwidth. `cpu_baseline` is
 the FP64 CPU oracle on a bounded sample of the same bed. `sort_every_step` times the same bed
-sorted by cell every step (the other schedule of this workload); `fp64_form` the FP64 form.
+sorted by cell every step (the other schedule of this workload); `fp64_form` the FP64 form;
+`adjoint` the forward (with checkpoints) and reverse sweeps on the 500k-parcel
+differentiation bed.
 
 --impl reference times the oracle itself (the slow program this build is checked
 against) on a bounded sample per step, with the same metric.
@@ -52,7 +54,9 @@ def parse():
     ap.add_argument("--sort-every", type=int, default=10)
     ap.add_argument("--precision", type=int, choices=(32, 64), default=32)
     ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64-form comparison (0 = skip)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--adjoint-steps", type=int, default=200,
+                    help="steps of the reverse-mode timing on the differentiation bed (0 = skip)")
     ap.add_argument("--sort1-steps", type=int, default=5,
                     help="steps of the sort-every-step measurement (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="parcels in the CPU-oracle sample")
@@ -153,8 +157,8 @@ def measured_peak():
 # parcel, from one ncu capture on the 128x128x128 / 8M-parcel dense bed
 # (profiles/k_cells_float_dense_8M.md); the dense bed's traffic grows in proportion to its
 # parcels. Reported only while the kernel source is the one captured.
-STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 66.25,
-                "source_sha256": "1f32740dcbce4636ff66f34dc3c8060e08069c43a0e15bddbe2c9fb3f2ca2819"}
+STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 66.0,
+                "source_sha256": "7bc1e819831d1d4d5732ff946b6b55a375059756c5e394757149e5fd8b90bed0"}
 
 
 def step_traffic(args, np_):
@@ -270,23 +274,36 @@ def run_gpu(args):
                                                         for k, v in pr1["ms"].items()}}
         b.tune(0, args.sort_every)
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: every step copies the parcel state in
+    # from pinned host memory and the new state and objectives back out; the copies of the
+    # arrays are spread over two copy streams (both directions), ordered around the step
     e2e = None
     if args.e2e_steps > 0:
         fields = mppic.PARCEL_FIELDS
         host = {k: parcels[k].cpu().pin_memory() for k in fields}
         out_host = {k: torch.empty_like(host[k]).pin_memory() for k in ("x", "y", "z", "u", "v", "w")}
         obj_host = torch.empty((1, 2), dtype=torch.float64).pin_memory()
+        copy_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.e2e_steps):
-            for k in fields:
-                parcels[k].copy_(host[k], non_blocking=True)
+            for cs in copy_streams:
+                cs.wait_stream(stream)
+            for i, k in enumerate(fields):
+                with torch.cuda.stream(copy_streams[i % 2]):
+                    parcels[k].copy_(host[k], non_blocking=True)
+            for cs in copy_streams:
+                stream.wait_stream(cs)
             o = b.step(parcels, gas, 1, obj[:1])
-            for k in out_host:
-                out_host[k].copy_(parcels[k], non_blocking=True)
+            for cs in copy_streams:
+                cs.wait_stream(stream)
+            for i, k in enumerate(out_host):
+                with torch.cuda.stream(copy_streams[i % 2]):
+                    out_host[k].copy_(parcels[k], non_blocking=True)
             obj_host.copy_(o, non_blocking=True)
+            for cs in copy_streams:
+                stream.wait_stream(cs)
         f1.record(stream)
         barrier()
         ems = f0.elapsed_time(f1)
@@ -296,7 +313,7 @@ def run_gpu(args):
         tsz = 4 if args.precision == 32 else 8
         e2e = {"value": world * bed.np * args.e2e_steps / (float(t2.item()) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": bed.np * 8 * tsz, "d2h_bytes_per_step": bed.np * 6 * tsz + 16,
-               "steps": args.e2e_steps}
+               "steps": args.e2e_steps, "copy_streams": len(copy_streams)}
         b.check()
 
     # FP64 form on the same bed, for the FP32-vs-FP64 comparison
@@ -326,6 +343,37 @@ def run_gpu(args):
         b64.close()
         del p64
 
+    # reverse mode on the differentiation bed (500k parcels, 32x32x128 cells): the forward
+    # steps with checkpoints every 20, then the gradient of a weighted sum of the two
+    # time-averaged objectives with respect to (C, s_d, u_in)
+    adj = None
+    if args.adjoint_steps > 0 and world == 1:
+        from paper_2211_15605_gb300 import synth
+        gb = synth.grad_bed()
+        adj = {"workload": "grad_32x32x128", "parcels": gb.np, "steps": args.adjoint_steps,
+               "checkpoint_every": 20}
+        for prec in (64, 32):
+            ba = mppic.Bed(gb.params, precision=prec, sort_every=10, stream=stream)
+            ba.checkpoint(20)
+            pa = mppic.parcels_to_device(gb.parcels, prec, device=dev)
+            ba.step(pa, None, 20)                # first use of the handle's scratch
+            ba.backward(1.0, 0.5)
+            pa = mppic.parcels_to_device(gb.parcels, prec, device=dev)
+            barrier()
+            a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a0.record(stream)
+            ba.step(pa, None, args.adjoint_steps)
+            a1.record(stream)
+            ba.backward(1.0, 0.5)                # synchronous
+            a2.record(stream)
+            barrier()
+            ba.check()
+            fw, bw = a0.elapsed_time(a1), a1.elapsed_time(a2)
+            adj[f"fp{prec}"] = {"forward_ms": round(fw, 3), "backward_ms": round(bw, 3),
+                                "backward_over_forward": round(bw / fw, 2)}
+            ba.close()
+            del pa
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(bed, args.cpu_sample, steps=2)
@@ -337,7 +385,7 @@ def run_gpu(args):
                 "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
                 "config": workload_config(bed, args), "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": prof["total_launches"], "clocks": clk,
-                "fp64_form": fp64, "sort_every_step": sort1,
+                "fp64_form": fp64, "sort_every_step": sort1, "adjoint": adj,
                 "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(line))
     b.close()
