@@ -130,6 +130,41 @@ __device__ __forceinline__ void bin3(const KParams<T>& p, T x, T y, T z, Cell3<T
   bin_axis(z, p.inv_d[2], p.inv_f[2], p.inv_lo[2], p.nz, c.k, c.xi[2]);
 }
 
+// In-cell coordinate of x on one axis if the binning formula puts x in cell ic there, with
+// the same value bin_axis would give; false if it does not, or (FP32 form) if x is within
+// the face margin where the FP64 formula must decide (the caller then uses bin_axis).
+__device__ __forceinline__ bool xi_in_cell(double x, double inv_d, float, float, int ic, double& xi) {
+  const double t = __dmul_rn(x, inv_d);
+  const double d = __dsub_rn(t, (double)ic);
+  if (!(d >= 0.0 && d < 1.0)) return false;
+  xi = d;
+  return true;
+}
+__device__ __forceinline__ bool xi_in_cell(float x, double, float inv_f, float inv_lo, int ic, float& xi) {
+  const float t = __fmul_rn(x, inv_f);
+  const float d = __fsub_rn(t, (float)ic);
+  const float tol = fabsf(t) * 2.5e-7f;
+  if (!(d >= tol && d <= 1.0f - tol)) return false;
+  const float lo = __fmaf_rn(x, inv_f, -t);
+  xi = __fadd_rn(__fadd_rn(d, lo), __fmul_rn(x, inv_lo));
+  return true;
+}
+
+// Binning of (x, y, z) when cell (i, j, k) is the likely answer: the in-cell test on each
+// axis, and the full formula only where it fails. Returns whether the cell is (i, j, k).
+template <class T>
+__device__ __forceinline__ bool bin3_expect(const KParams<T>& p, T x, T y, T z, int i, int j, int k,
+                                            Cell3<T>& c) {
+  if (xi_in_cell(x, p.inv_d[0], p.inv_f[0], p.inv_lo[0], i, c.xi[0]) &&
+      xi_in_cell(y, p.inv_d[1], p.inv_f[1], p.inv_lo[1], j, c.xi[1]) &&
+      xi_in_cell(z, p.inv_d[2], p.inv_f[2], p.inv_lo[2], k, c.xi[2])) {
+    c.i = i; c.j = j; c.k = k;
+    return true;
+  }
+  bin3(p, x, y, z, c);
+  return c.i == i && c.j == j && c.k == k;
+}
+
 template <class T>
 __device__ __forceinline__ int cell_id(const KParams<T>& p, int i, int j, int k) {
   return i + p.nx * (j + p.ny * k);
@@ -1077,8 +1112,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
       const T x = slot[0], y = slot[BCELLS], z = slot[2 * BCELLS];
       const T d = slot[6 * BCELLS], om = slot[7 * BCELLS];
       Cell3<T> c;
-      bin3(p, x, y, z, c);
-      const bool own = c.i == ci && c.j == cj && c.k == ck;
+      const bool own = bin3_expect(p, x, y, z, ci, cj, ck, c);
       const T V = om * (d * d * d) * p.vcoef;
       if (MODE == 0) {
         if (own) {
@@ -1145,9 +1179,8 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         }
         if (bad) atomicOr(p.errs, ERR_DOMAIN);
         Cell3<T> cn;
-        bin3(p, pos[0], pos[1], pos[2], cn);
         // solids volume of the new position, for the next step
-        if (cn.i == ci && cn.j == cj && cn.k == ck) {
+        if (bin3_expect(p, pos[0], pos[1], pos[2], ci, cj, ck, cn)) {
           T Wq[8];
           corner_weights(cn.xi, Wq);
 #pragma unroll
