@@ -854,33 +854,107 @@ __device__ __noinline__ void deposit_foreign(const KParams<T>& p, u64* fx, int* 
   }
 }
 
-// Trilinear weights of in-cell coordinates xi: corner weights W[a + 2b + 4c], the y-z
-// products yz[b + 2c] they are built from (also the weights of d/dx of the interpolant),
-// and xi itself (the other two gradient weights are formed where they are used).
-template <class T>
-struct Weights {
-  T W[8], yz[4], xi[3];
+// Trilinear corner weights W[a + 2b + 4c] of in-cell coordinates xi. FP64: 8 values. FP32:
+// 4 pairs (corners 2k and 2k+1, which differ in the x factor), formed and used with the
+// paired FP32 operations (each lane one rounded product or fused multiply-add, so the values
+// equal the scalar ones).
+template <class T> struct W8;
+template <> struct W8<double> {
+  double w[8];
+  __device__ __forceinline__ double get(int q) const { return w[q]; }
+};
+template <> struct W8<float> {
+  float2 w[4];
+  __device__ __forceinline__ float get(int q) const { return (q & 1) ? w[q >> 1].y : w[q >> 1].x; }
 };
 
+// The weights and the y-z products yz[b + 2c] they are built from (also the weights of d/dx
+// of the interpolant), and xi (the other two gradient weights are formed where they are used).
 template <class T>
-__device__ __forceinline__ void corner_weights(const T (&xi)[3], T (&W)[8]) {
-  const T w0[2] = {T(1) - xi[0], xi[0]}, w1[2] = {T(1) - xi[1], xi[1]}, w2[2] = {T(1) - xi[2], xi[2]};
-  T yz[4];
+struct Weights {
+  W8<T> W;
+  T yz[4], xi[3];
+};
+
+__device__ __forceinline__ void corner_weights(const double (&xi)[3], W8<double>& W, double (&yz)[4]) {
+  const double w0[2] = {1.0 - xi[0], xi[0]}, w1[2] = {1.0 - xi[1], xi[1]}, w2[2] = {1.0 - xi[2], xi[2]};
 #pragma unroll
   for (int q = 0; q < 4; ++q) yz[q] = w1[q & 1] * w2[q >> 1];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) W[q] = w0[q & 1] * yz[q >> 1];
+  for (int q = 0; q < 8; ++q) W.w[q] = w0[q & 1] * yz[q >> 1];
+}
+__device__ __forceinline__ void corner_weights(const float (&xi)[3], W8<float>& W, float (&yz)[4]) {
+  const float2 wx = make_float2(1.0f - xi[0], xi[0]), wy = make_float2(1.0f - xi[1], xi[1]);
+  const float z0 = 1.0f - xi[2], z1 = xi[2];
+  const float2 yz01 = __fmul2_rn(wy, make_float2(z0, z0));   // yz[0], yz[1]
+  const float2 yz23 = __fmul2_rn(wy, make_float2(z1, z1));   // yz[2], yz[3]
+  yz[0] = yz01.x; yz[1] = yz01.y; yz[2] = yz23.x; yz[3] = yz23.y;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) W.w[k] = __fmul2_rn(wx, make_float2(yz[k], yz[k]));
 }
 
 template <class T>
 __device__ __forceinline__ void all_weights(const T (&xi)[3], Weights<T>& r) {
-  const T w0[2] = {T(1) - xi[0], xi[0]}, w1[2] = {T(1) - xi[1], xi[1]}, w2[2] = {T(1) - xi[2], xi[2]};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) r.yz[q] = w1[q & 1] * w2[q >> 1];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) r.W[q] = w0[q & 1] * r.yz[q >> 1];
+  corner_weights(xi, r.W, r.yz);
   r.xi[0] = xi[0]; r.xi[1] = xi[1]; r.xi[2] = xi[2];
 }
+
+// The 40 per-cell register sums of the cell kernel: the solids volume and the drag sums A,
+// Bx, By, Bz at the cell's 8 corners.
+template <class T> struct CellSums;
+template <> struct CellSums<double> {
+  double v[NQ][8];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[q][k] = 0.0;
+  }
+  __device__ __forceinline__ void add_vol(double V, const W8<double>& W) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[0][k] += V * W.w[k];
+  }
+  __device__ __forceinline__ void add_drag(double f, double fu0, double fu1, double fu2,
+                                           const W8<double>& W) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v[1][k] += f * W.w[k];
+      v[2][k] += fu0 * W.w[k];
+      v[3][k] += fu1 * W.w[k];
+      v[4][k] += fu2 * W.w[k];
+    }
+  }
+  __device__ __forceinline__ double get(int q, int k) const { return v[q][k]; }
+};
+template <> struct CellSums<float> {
+  float2 v[NQ][4];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[q][k] = make_float2(0.0f, 0.0f);
+  }
+  __device__ __forceinline__ void add_vol(float V, const W8<float>& W) {
+    const float2 s = make_float2(V, V);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[0][k] = __ffma2_rn(s, W.w[k], v[0][k]);
+  }
+  __device__ __forceinline__ void add_drag(float f, float fu0, float fu1, float fu2,
+                                           const W8<float>& W) {
+    const float2 s1 = make_float2(f, f), s2 = make_float2(fu0, fu0), s3 = make_float2(fu1, fu1),
+                 s4 = make_float2(fu2, fu2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[1][k] = __ffma2_rn(s1, W.w[k], v[1][k]);
+      v[2][k] = __ffma2_rn(s2, W.w[k], v[2][k]);
+      v[3][k] = __ffma2_rn(s3, W.w[k], v[3][k]);
+      v[4][k] = __ffma2_rn(s4, W.w[k], v[4][k]);
+    }
+  }
+  __device__ __forceinline__ float get(int q, int k) const {
+    return (k & 1) ? v[q][k >> 1].y : v[q][k >> 1].x;
+  }
+};
 
 // Interpolation at one parcel from the brick's node-field tile (corner (0,0,0) at tile node
 // base) with precomputed weights. The gradient of the trilinear interpolant of tau is
@@ -897,15 +971,16 @@ __device__ __forceinline__ void interp_tile_w(const KParams<T>& p, const T* t, i
   for (int q = 0; q < 8; ++q) {
     T v[8];
     tile_node(t, base + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2)), gpf, v);
-    r.es += w.W[q] * v[0];
-    r.ug[0] += w.W[q] * v[1];
-    r.ug[1] += w.W[q] * v[2];
-    r.ug[2] += w.W[q] * v[3];
+    const T Wq = w.W.get(q);
+    r.es += Wq * v[0];
+    r.ug[0] += Wq * v[1];
+    r.ug[1] += Wq * v[2];
+    r.ug[2] += Wq * v[3];
     tau[q] = v[4];
     if (gpf) {
-      r.gp[0] += w.W[q] * v[5];
-      r.gp[1] += w.W[q] * v[6];
-      r.gp[2] += w.W[q] * v[7];
+      r.gp[0] += Wq * v[5];
+      r.gp[1] += Wq * v[6];
+      r.gp[2] += Wq * v[7];
     }
   }
   if (!gpf) { r.gp[0] = p.gp[0]; r.gp[1] = p.gp[1]; r.gp[2] = p.gp[2]; }
@@ -1074,9 +1149,8 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   const int nmax = __reduce_max_sync(FULL, n);
   int off = p.cstart[kbase];                     // the group's first parcel
   for (int w = 0; w < warp; ++w) off += s_wsum[w];
-  T aV[8], aA[8], aB[3][8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) { aV[q] = 0; aA[q] = 0; aB[0][q] = 0; aB[1][q] = 0; aB[2][q] = 0; }
+  CellSums<T> sums;
+  sums.zero();
   T o_dp = 0, o_hn = 0, o_vs = 0;
 
   // Level r's parcel values are copied into this thread's slots of stage r % PSTAGES
@@ -1116,10 +1190,10 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
       const T V = om * (d * d * d) * p.vcoef;
       if (MODE == 0) {
         if (own) {
-          T Wq[8];
-          corner_weights(c.xi, Wq);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) aV[k] += V * Wq[k];
+          W8<T> Wq;
+          T yz[4];
+          corner_weights(c.xi, Wq, yz);
+          sums.add_vol(V, Wq);
         } else {
           deposit_foreign<T, 1>(p, fx, s_kr, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 0,
                                 V, T(0), T(0), T(0));
@@ -1149,14 +1223,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         o_vs += V;
         // drag sums of the pre-push state, at the old position
         if (own) {
-          const T fu0 = f * u, fu1 = f * v, fu2 = f * w;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            aA[k] += f * wt.W[k];
-            aB[0][k] += fu0 * wt.W[k];
-            aB[1][k] += fu1 * wt.W[k];
-            aB[2][k] += fu2 * wt.W[k];
-          }
+          sums.add_drag(f, f * u, f * v, f * w, wt.W);
         } else {
           deposit_foreign<T, 4>(p, fx, s_kr, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 1,
                                 f, f * u, f * v, f * w);
@@ -1181,10 +1248,10 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         Cell3<T> cn;
         // solids volume of the new position, for the next step
         if (bin3_expect(p, pos[0], pos[1], pos[2], ci, cj, ck, cn)) {
-          T Wq[8];
-          corner_weights(cn.xi, Wq);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) aV[k] += V * Wq[k];
+          W8<T> Wq;
+          T yz[4];
+          corner_weights(cn.xi, Wq, yz);
+          sums.add_vol(V, Wq);
         } else {
           deposit_foreign<T, 1>(p, fx, s_kr, bi0, bj0, bk0, cn.i, cn.j, cn.k, cn.xi[0], cn.xi[1],
                                 cn.xi[2], 0, V, T(0), T(0), T(0));
@@ -1216,12 +1283,10 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     __syncthreads();
     if (n > 0) {
       const int tn = tn0 + (k & 1) + TX * (((k >> 1) & 1) + TY * (k >> 2));
-      tile[tn] += aV[k];
+      tile[tn] += sums.get(0, k);
       if (MODE == 1) {
-        tile[TNODES + tn] += aA[k];
-        tile[2 * TNODES + tn] += aB[0][k];
-        tile[3 * TNODES + tn] += aB[1][k];
-        tile[4 * TNODES + tn] += aB[2][k];
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) tile[q * TNODES + tn] += sums.get(q, k);
       }
     }
   }
