@@ -1000,6 +1000,52 @@ __device__ __forceinline__ void interp_tile_w(const KParams<T>& p, const T* t, i
   r.gt[2] = gz * p.invh[2];
 }
 
+// The same interpolation in the FP32 form with paired operations: (eps_s, u_g,x) and
+// (u_g,y, u_g,z) are summed as two pairs per corner, and the x and y components of the
+// stress gradient as one pair (each lane one rounded operation: the scalar values).
+__device__ __forceinline__ void interp_tile_w(const KParams<float>& p, const float* t, int base,
+                                              const Weights<float>& w, Interp<float>& r) {
+  float2 e0 = make_float2(0.0f, 0.0f), e1 = make_float2(0.0f, 0.0f), g01 = make_float2(0.0f, 0.0f);
+  float g2 = 0.0f;
+  float tau[8];
+  const bool gpf = p.has_gp != 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int n = base + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2));
+    const float4 a = *reinterpret_cast<const float4*>(t + 4 * n);
+    const float Wq = w.W.get(q);
+    const float2 W2 = make_float2(Wq, Wq);
+    e0 = __ffma2_rn(W2, make_float2(a.x, a.y), e0);
+    e1 = __ffma2_rn(W2, make_float2(a.z, a.w), e1);
+    tau[q] = t[8 * TNODES + n];
+    if (gpf) {
+      const float4 g = *reinterpret_cast<const float4*>(t + 4 * (TNODES + n));
+      g01 = __ffma2_rn(W2, make_float2(g.x, g.y), g01);
+      g2 += Wq * g.z;
+    }
+  }
+  r.es = e0.x; r.ug[0] = e0.y; r.ug[1] = e1.x; r.ug[2] = e1.y;
+  if (gpf) { r.gp[0] = g01.x; r.gp[1] = g01.y; r.gp[2] = g2; }
+  else { r.gp[0] = p.gp[0]; r.gp[1] = p.gp[1]; r.gp[2] = p.gp[2]; }
+  float2 gxy = make_float2(0.0f, 0.0f);
+  float gz = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int u0 = q & 1, u1 = q >> 1;
+    const float wx = u0 ? w.xi[0] : 1.0f - w.xi[0];
+    const float wy = u1 ? w.xi[1] : 1.0f - w.xi[1];
+    const float wz = u1 ? w.xi[2] : 1.0f - w.xi[2];
+    const float2 dxy = __fadd2_rn(make_float2(tau[1 + 2 * u0 + 4 * u1], tau[u0 + 2 + 4 * u1]),
+                                  make_float2(-tau[2 * u0 + 4 * u1], -tau[u0 + 4 * u1]));
+    gxy = __ffma2_rn(dxy, make_float2(w.yz[q], wx * wz), gxy);
+    gz += (tau[u0 + 2 * u1 + 4] - tau[u0 + 2 * u1]) * (wx * wy);
+  }
+  const float2 gt = __fmul2_rn(gxy, make_float2(p.invh[0], p.invh[1]));
+  r.gt[0] = gt.x;
+  r.gt[1] = gt.y;
+  r.gt[2] = gz * p.invh[2];
+}
+
 // Wen-Yu drag coefficient in the FP32 form: the two powers of the voidage share one log2.
 __device__ __forceinline__ float wen_yu_step(const KParams<float>& p, float d, float es,
                                              const float (&s)[3]) {
