@@ -52,6 +52,9 @@ struct mppic_handle {
   void* fld = nullptr;       // 5 x nnode T
   int* cstart = nullptr;     // nkeys + 1
   uint8_t* cellmap = nullptr;  // nbricks * 256: cells ranked by parcel count per brick
+  u64* bacc = nullptr;         // [nbricks][NQ][words][TNODES]: bricks' tile slots
+  int* bstamp = nullptr;       // [nbricks]: deposit epoch of each slot
+  int* epoch = nullptr;        // the current deposit epoch (device counter)
   double* obj_part = nullptr;  // 3 x nbricks
   double* obj_tmp = nullptr;   // 2 doubles (objectives when the caller passes none)
   double* obj_slices = nullptr;  // 3 x OBJ_BLOCKS slice partials of the objective reduction
@@ -225,6 +228,9 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   p.zr = h->zr;
   p.cstart = h->cstart;
   p.cellmap = h->cellmap;
+  p.bacc = h->bacc;
+  p.bstamp = h->bstamp;
+  p.epoch = h->epoch;
   return p;
 }
 
@@ -244,6 +250,7 @@ mppic_status upload_beds(mppic_handle* h, const mppic_gas* gas, const KParams<T>
     tmp.nnode = h->noff[b + 1] - h->noff[b];
     tmp.nbricks = h->boff[b + 1] - h->boff[b];
     tmp.fld = h->fld; tmp.acc = h->acc; tmp.errs = h->errs; tmp.cstart = h->cstart; tmp.cellmap = h->cellmap; tmp.zr = h->zr;
+    tmp.bacc = h->bacc; tmp.bstamp = h->bstamp; tmp.epoch = h->epoch;
     KParams<T> p = make_params<T>(&tmp, nullptr);
     p.nbase = h->noff[b];
     p.bbase = h->boff[b];
@@ -260,6 +267,7 @@ mppic_status upload_beds(mppic_handle* h, const mppic_gas* gas, const KParams<T>
       }
     }
     tmp.fld = nullptr; tmp.acc = nullptr; tmp.errs = nullptr; tmp.cstart = nullptr; tmp.cellmap = nullptr; tmp.zr = nullptr;
+    tmp.bacc = nullptr; tmp.bstamp = nullptr; tmp.epoch = nullptr;
     v[b] = p;
   }
   const size_t bytes = sizeof(KParams<T>) * h->nbeds;
@@ -402,15 +410,35 @@ mppic_status launch_finalize(mppic_handle* h, const KParams<T>& p, double* vs_ou
   unsigned g = blocks(h->nnode, 256);
   if (g > 152u * 8u) g = 152u * 8u;
   if (beds) {                  // a batch: every node of every bed
-    ph.launched(1);
+    ph.launched(2);
     k_finalize_b<T><<<g, 256, 0, h->stream>>>(beds, h->d_noff, h->nbeds, h->nnode);
+    LAUNCHED();
+    k_epoch_next<<<1, 1, 0, h->stream>>>(h->epoch);
     LAUNCHED();
     return MPPIC_OK;
   }
   ph.launched(2);
   k_finalize<T><<<g, 256, 0, h->stream>>>(p, vs_out, full ? 1 : 0);
   LAUNCHED();
-  k_range_roll<<<1, 1, 0, h->stream>>>(h->zr);
+  k_range_roll<<<1, 1, 0, h->stream>>>(h->zr, h->epoch);
+  LAUNCHED();
+  return MPPIC_OK;
+}
+
+// After the last step of a call: the bricks' drag sums into the global accumulators (for
+// the drag-sum output), then the next epoch.
+template <class T>
+mppic_status launch_drag_fold(mppic_handle* h, const KParams<T>& p, const KParams<T>* beds) {
+  Phase ph(h, PH_FINALIZE);
+  ph.launched(2);
+  unsigned g = blocks(h->nnode, 256);
+  if (g > 152u * 8u) g = 152u * 8u;
+  if (beds)
+    k_drag_fold_b<T><<<g, 256, 0, h->stream>>>(beds, h->d_noff, h->nbeds, h->nnode);
+  else
+    k_drag_fold<T><<<g, 256, 0, h->stream>>>(p);
+  LAUNCHED();
+  k_epoch_next<<<1, 1, 0, h->stream>>>(h->epoch);
   LAUNCHED();
   return MPPIC_OK;
 }
@@ -581,6 +609,13 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
             obj_out ? obj_out + 2 * it : h->obj_tmp);
       LAUNCHED();
     }
+  }
+  if (nsteps > 0) {              // the last step's drag sums, complete, for the drag-sum output
+    s = launch_drag_fold<T>(h, p, beds);
+    if (s) return s;
+  } else {                       // the call-start deposit's tile slots are not consumed
+    k_epoch_next<<<1, 1, 0, h->stream>>>(h->epoch);
+    LAUNCHED();
   }
   if ((nsteps == 0 || beds) && pc->cell && np > 0) {
     if (beds)
@@ -873,10 +908,16 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
       alloc((void**)&h->zr, sizeof(int) * 4) && alloc((void**)&h->wq, sizeof(unsigned long long)) &&
       alloc((void**)&h->totals, sizeof(uint32_t) * 256) &&
       alloc((void**)&h->cellmap, (size_t)BCELLS * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->bacc, sizeof(u64) * NQ * h->words * TNODES * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->bstamp, sizeof(int) * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->epoch, sizeof(int)) &&
       alloc((void**)&h->obj_slices, sizeof(double) * 3 * OBJ_BLOCKS) &&
       alloc((void**)&h->obj_count, sizeof(unsigned))) {
     cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(u64) * NQ * h->words * nnode, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->obj_count, 0, sizeof(unsigned), h->stream);
+    // no tile slot is valid yet: stamps -1, epoch 0
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->bstamp, 0xff, sizeof(int) * (nbricks > 0 ? nbricks : 1), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->epoch, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) {                      // identity cell map until the first sort
       std::vector<uint8_t> id((size_t)BCELLS * (nbricks > 0 ? nbricks : 1));
       for (size_t i = 0; i < id.size(); ++i) id[i] = (uint8_t)(i % BCELLS);
@@ -1127,6 +1168,7 @@ void mppic_destroy(mppic_handle* h) {
   cudaFree(h->acc); cudaFree(h->fld); cudaFree(h->cstart); cudaFree(h->obj_part);
   cudaFree(h->obj_tmp); cudaFree(h->errs); cudaFree(h->zr); cudaFree(h->totals); cudaFree(h->hist);
   cudaFree(h->obj_slices); cudaFree(h->obj_count); cudaFree(h->cellmap);
+  cudaFree(h->bacc); cudaFree(h->bstamp); cudaFree(h->epoch);
   for (int i = 0; i < 2; ++i) { cudaFree(h->keys[i]); cudaFree(h->vals[i]); }
   for (int f = 0; f < 8; ++f) cudaFree(h->sorted[f]);
   cudaFree(h->sorted_pid);

@@ -72,6 +72,10 @@ struct KParams {
   const int* cstart;         // [nkeys+1]: first sorted parcel of each brick-major key
   const uint8_t* cellmap;    // [nbricks*256]: local cell of thread t of each brick (own
                              // order, or ranked by parcel count; chosen at the last sort)
+  u64* bacc;                 // [nbricks][NQ][words][TNODES]: each brick's node tile of the
+                             // last deposit that covered it, in fixed point
+  int* bstamp;               // [nbricks]: deposit epoch that wrote the brick's tile
+  int* epoch;                // the current deposit epoch (advanced after each node pass)
 };
 
 template <class T> struct Words;
@@ -1135,6 +1139,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   int cur_bed = -1;
   const bool copy_ro = src.a[0] != dst.a[0];
   const int nq = MODE == 1 ? NQ : 1;
+  const int epoch = *(beds ? beds[0].epoch : p0.epoch);
 
   for (long long iter = 0; iter < total_bricks; ++iter) {
   __syncthreads();
@@ -1338,15 +1343,15 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   }
   __syncthreads();
   if (tid == 0 && s_kr[1] >= 0) { atomicMin(&p.zr[0], s_kr[0]); atomicMax(&p.zr[1], s_kr[1]); }
-  // ---- the tile in exact fixed point, plus the off-cell contributions, to the global
-  // accumulators
-  for (int tn = tid; tn < TNODES; tn += BCELLS) {
-    const int i = bi0 + tn % TX, j = bj0 + (tn / TX) % TY, k = bk0 + tn / (TX * TY);
-    if (i > p.nx || j > p.ny || k > p.nz) continue;
-    const long long gn = p.nbase + node_id(p, i, j, k);
-    for (int qq = 0; qq < nq; ++qq) {
+  // ---- the tile in exact fixed point, plus the off-cell contributions, to the brick's slot
+  // (plain stores; the node pass after the step adds the slots of the bricks that share a
+  // node), stamped with this deposit's epoch
+  {
+    u64* slot = p.bacc + b * (long long)(NQ * W * TNODES);
+    for (int e = tid; e < nq * TNODES; e += BCELLS) {
+      const int qq = e / TNODES, tn = e % TNODES;
       u64 f[W];
-      to_fixed(tile[qq * TNODES + tn], qq == 0 ? p.mV : p.mA, f, p.errs);
+      to_fixed(tile[e], qq == 0 ? p.mV : p.mA, f, p.errs);
       u64 carry = 0;
 #pragma unroll
       for (int w = 0; w < W; ++w) {
@@ -1355,18 +1360,51 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         const u64 c1 = s0 < g ? 1ull : 0ull;
         f[w] = s0 + carry;
         carry = c1 + (f[w] < s0 ? 1ull : 0ull);
+        slot[(qq * W + w) * TNODES + tn] = f[w];
       }
-      acc_add(p.acc + (long long)(qq * W) * p.nstride + gn, p.nstride, f);
     }
+    if (tid == 0) p.bstamp[b] = epoch;
   }
   if (MODE == 1) cta_sum3(o_dp, o_hn, o_vs, red, obj_part + 3 * b);
   }  // persistent loop
 }
 
+// Fixed-point value of quantity q at node (i, j, k) of a bed: the global accumulator (the
+// off-brick deposits) plus the tile slots of the bricks (at most 2 per axis) whose tile
+// holds the node and that were written in deposit epoch ep.
+template <class T>
+__device__ __forceinline__ void node_sum(const KParams<T>& p, int ep, int q, long long n, int i,
+                                         int j, int k, u64 (&f)[Words<T>::n]) {
+  constexpr int W = Words<T>::n;
+#pragma unroll
+  for (int w = 0; w < W; ++w) f[w] = p.acc[(long long)(q * W + w) * p.nstride + p.nbase + n];
+  const int bx1 = min(i / BX, p.nbx - 1), by1 = min(j / BY, p.nby - 1), bz1 = min(k / BZ, p.nbz - 1);
+  const int bx0 = (i % BX == 0 && i > 0) ? i / BX - 1 : bx1;
+  const int by0 = (j % BY == 0 && j > 0) ? j / BY - 1 : by1;
+  const int bz0 = (k % BZ == 0 && k > 0) ? k / BZ - 1 : bz1;
+  for (int bz = bz0; bz <= bz1; ++bz)
+    for (int by = by0; by <= by1; ++by)
+      for (int bx = bx0; bx <= bx1; ++bx) {
+        const long long b = p.bbase + bx + (long long)p.nbx * (by + (long long)p.nby * bz);
+        if (p.bstamp[b] != ep) continue;
+        const int tn = (i - bx * BX) + TX * ((j - by * BY) + TY * (k - bz * BZ));
+        const u64* slot = p.bacc + b * (long long)(NQ * W * TNODES);
+        u64 carry = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const u64 g = slot[(q * W + w) * TNODES + tn];
+          const u64 s0 = f[w] + g;
+          const u64 c1 = s0 < g ? 1ull : 0ull;
+          f[w] = s0 + carry;
+          carry = c1 + (f[w] < s0 ? 1ull : 0ull);
+        }
+      }
+}
+
 // a5: node fields from the deposited volume. Reads and clears the Vs accumulator and
 // clears the drag-sum accumulators for the coming push. vs_out (nullable) receives Vs.
 template <class T>
-__device__ __forceinline__ void finalize_node(const KParams<T>& p, int n, int i, int j, int k,
+__device__ __forceinline__ void finalize_node(const KParams<T>& p, int ep, int n, int i, int j, int k,
                                               double* vs_out);
 
 template <class T>
@@ -1379,24 +1417,52 @@ __global__ void k_finalize(KParams<T> p, double* __restrict__ vs_out, int full) 
     khi = min(p.nz, max(p.zr[1], p.zr[3]));
   }
   const int n0 = klo * layer, n1 = (khi + 1) * layer;
+  const int ep = *p.epoch;
   for (int n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += gridDim.x * blockDim.x)
-    finalize_node(p, n, n % nx1, (n / nx1) % ny1, n / layer, vs_out);
+    finalize_node(p, ep, n, n % nx1, (n / nx1) % ny1, n / layer, vs_out);
 }
 
-// Moves the deposit's layer range to "last finalized" and empties it for the next deposit.
-__global__ void k_range_roll(int* zr) {
+// Moves the deposit's layer range to "last finalized" and empties it for the next deposit,
+// and advances the deposit epoch (the tile slots written so far are consumed).
+__global__ void k_range_roll(int* zr, int* epoch) {
   zr[2] = zr[0];
   zr[3] = zr[1];
   zr[0] = 1 << 30;
   zr[1] = -1;
+  *epoch += 1;
+}
+
+__global__ void k_epoch_next(int* epoch) { *epoch += 1; }
+
+// After the last step of a call: the drag sums A, B of the bricks' tile slots are added to
+// the global accumulators (which then hold the step's complete sums, read by the drag-sum
+// output until the next node pass clears them). Layers of the last deposit only.
+template <class T>
+__global__ void k_drag_fold(KParams<T> p) {
+  constexpr int W = Words<T>::n;
+  const int nx1 = p.nx + 1, ny1 = p.ny + 1;
+  const int layer = nx1 * ny1;
+  const int klo = max(0, p.zr[0]), khi = min(p.nz, p.zr[1]);
+  if (khi < klo) return;
+  const int ep = *p.epoch;
+  for (int n = klo * layer + blockIdx.x * blockDim.x + threadIdx.x; n < (khi + 1) * layer;
+       n += gridDim.x * blockDim.x) {
+    const int i = n % nx1, j = (n / nx1) % ny1, k = n / layer;
+    for (int q = 1; q < NQ; ++q) {
+      u64 f[W];
+      node_sum(p, ep, q, n, i, j, k, f);
+#pragma unroll
+      for (int w = 0; w < W; ++w) p.acc[(long long)(q * W + w) * p.nstride + p.nbase + n] = f[w];
+    }
+  }
 }
 
 template <class T>
-__device__ __forceinline__ void finalize_node(const KParams<T>& p, int n, int i, int j, int k,
+__device__ __forceinline__ void finalize_node(const KParams<T>& p, int ep, int n, int i, int j, int k,
                                               double* vs_out) {
   constexpr int W = Words<T>::n;
   u64 fx[W];
-  for (int w = 0; w < W; ++w) { fx[w] = p.acc[(long long)w * p.nstride + p.nbase + n]; }
+  node_sum(p, ep, 0, n, i, j, k, fx);
   if (W == 1 && (long long)fx[0] >= (1ll << 62)) atomicOr(p.errs, ERR_RANGE);
   double Vs = from_fixed(fx, p.inv_mV);
   for (int e = 0; e < NQ * W; ++e) p.acc[(long long)e * p.nstride + p.nbase + n] = 0;
@@ -1549,13 +1615,36 @@ __global__ void k_bin_b(const KParams<T>* __restrict__ beds, const long long* __
 template <class T>
 __global__ void k_finalize_b(const KParams<T>* __restrict__ beds, const long long* __restrict__ noff,
                              int nbeds, long long total) {
+  const int ep = *beds[0].epoch;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
     const int bed = find_bed(noff, nbeds, g);
     const KParams<T>& p = beds[bed];
     const int n = (int)(g - noff[bed]);
     const int nx1 = p.nx + 1, ny1 = p.ny + 1;
-    finalize_node(p, n, n % nx1, (n / nx1) % ny1, n / (nx1 * ny1), (double*)nullptr);
+    finalize_node(p, ep, n, n % nx1, (n / nx1) % ny1, n / (nx1 * ny1), (double*)nullptr);
+  }
+}
+
+// k_drag_fold for a batch: every node of every bed.
+template <class T>
+__global__ void k_drag_fold_b(const KParams<T>* __restrict__ beds, const long long* __restrict__ noff,
+                              int nbeds, long long total) {
+  constexpr int W = Words<T>::n;
+  const int ep = *beds[0].epoch;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int bed = find_bed(noff, nbeds, g);
+    const KParams<T>& p = beds[bed];
+    const int n = (int)(g - noff[bed]);
+    const int nx1 = p.nx + 1, ny1 = p.ny + 1;
+    const int i = n % nx1, j = (n / nx1) % ny1, k = n / (nx1 * ny1);
+    for (int q = 1; q < NQ; ++q) {
+      u64 f[W];
+      node_sum(p, ep, q, n, i, j, k, f);
+#pragma unroll
+      for (int w = 0; w < W; ++w) p.acc[(long long)(q * W + w) * p.nstride + p.nbase + n] = f[w];
+    }
   }
 }
 
