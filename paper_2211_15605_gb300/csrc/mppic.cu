@@ -17,6 +17,7 @@
 #include "../../include/mppic.h"
 #include "mppic_adjoint.cuh"
 #include "mppic_device.cuh"
+#include "mppic_resort.cuh"
 
 using namespace mppic;
 
@@ -67,6 +68,17 @@ struct mppic_handle {
   uint32_t* vals[2] = {nullptr, nullptr};
   uint32_t* hist = nullptr;
   uint32_t* totals = nullptr;
+  uint8_t* bcell[2] = {nullptr, nullptr};  // local re-sort: cell bytes of the bucket and its copy
+  // local re-sort, per brick (see mppic_resort.cuh)
+  int4* bgeo = nullptr;        // {first brick of the bed, nbx, nby, nbz}
+  uint32_t* rs_cnt = nullptr;  // [nbricks][27] parcels of the source brick per neighbour slot
+  uint32_t* rs_off = nullptr;  // [nbricks][27] first bucket position of each run
+  uint32_t* rs_wcnt = nullptr; // [nbricks][8][27] the same counts per warp segment
+  int* rs_far = nullptr;       // parcels arriving from beyond the neighbours
+  int* rs_far_next = nullptr;  // next free position of the far parcels
+  int* rs_count = nullptr;     // bucket size
+  int* rs_start = nullptr;     // bucket start
+  int* rs_part = nullptr;      // bucket sizes summed over each CTA's bricks
   void* sorted[8] = {};
   int* sorted_pid = nullptr;
   bool sorted_pid_ok = false;
@@ -321,8 +333,9 @@ mppic_status ensure_capacity(mppic_handle* h, long long np, bool want_pid) {
   long long cap = np > h->cap ? np : h->cap;
   if (cap > h->cap) {
     for (int i = 0; i < 2; ++i) {
-      cudaFree(h->keys[i]); cudaFree(h->vals[i]);
+      cudaFree(h->keys[i]); cudaFree(h->vals[i]); cudaFree(h->bcell[i]);
       h->keys[i] = h->vals[i] = nullptr;
+      h->bcell[i] = nullptr;
     }
     cudaFree(h->hist); h->hist = nullptr;
     for (int f = 0; f < 8; ++f) { cudaFree(h->sorted[f]); h->sorted[f] = nullptr; }
@@ -332,6 +345,7 @@ mppic_status ensure_capacity(mppic_handle* h, long long np, bool want_pid) {
     for (int i = 0; i < 2; ++i) {
       CU(cudaMalloc(&h->keys[i], sizeof(uint32_t) * cap));
       CU(cudaMalloc(&h->vals[i], sizeof(uint32_t) * cap));
+      CU(cudaMalloc(&h->bcell[i], cap));
     }
     CU(cudaMalloc(&h->hist, sizeof(uint32_t) * 256 * (nblk > 0 ? nblk : 1)));
     for (int f = 0; f < 8; ++f) CU(cudaMalloc(&h->sorted[f], h->tsize * cap));
@@ -345,7 +359,7 @@ mppic_status ensure_capacity(mppic_handle* h, long long np, bool want_pid) {
 // copy, and rebuild the cell ranges. Leaves the sorted copy as the parcel source.
 template <class T>
 mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays<T> cur,
-                               bool keys_ready = false) {
+                               bool keys_ready = false, bool local = false) {
   const long long np = pc->np;
   mppic_status s = ensure_capacity(h, np, pc->pid != nullptr);
   if (s) return s;
@@ -363,6 +377,31 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
       else
         k_keys<T><<<blocks(np, 256), 256, 0, st>>>(p, cur.a[0], cur.a[1], cur.a[2], h->keys[0], np);
       LAUNCHED();
+    }
+    if (local) {                // `cur` is laid out by the current cell starts
+      const long long nb = h->nbricks;
+      const unsigned gb = (unsigned)(nb < 8LL * h->nsm ? nb : 8LL * h->nsm);
+      CU(cudaMemsetAsync(h->rs_far, 0, sizeof(int) * nb, st));
+      k_rs_hist<<<gb, RS_THREADS, 0, st>>>(h->keys[0], h->cstart, h->bgeo, nb, h->rs_cnt,
+                                           h->rs_wcnt, h->rs_far);
+      k_rs_count<<<blocks(nb, RS_THREADS), RS_THREADS, 0, st>>>(h->rs_cnt, h->rs_far, h->bgeo, nb,
+                                                                h->rs_count, h->rs_part);
+      k_rs_offsets<<<blocks(nb, RS_THREADS), RS_THREADS, 0, st>>>(
+          h->rs_cnt, h->rs_count, h->rs_part, h->bgeo, nb, h->rs_start, h->rs_off,
+          h->rs_far_next, h->cstart + h->nkeys);
+      // the hist pass read the old brick ranges; the scatter reads them too, the build
+      // rewrites them
+      k_rs_scatter<<<gb, RS_THREADS, 0, st>>>(h->keys[0], h->cstart, h->bgeo, nb, h->rs_off,
+                                              h->rs_wcnt, h->rs_far_next, h->keys[1], h->bcell[0]);
+      k_rs_build<T><<<(unsigned)nb, RS_THREADS, 0, st>>>(
+          cur, sorted_arrays<T>(h, cur.pid != nullptr, cur.tag != nullptr), h->rs_start,
+          h->rs_count, h->rs_far, h->keys[1], h->bcell[0], h->vals[0], h->bcell[1], h->cstart,
+          h->cellmap);
+      LAUNCHED();
+      ph.launched(keys_ready ? 5 : 6);
+      h->order_np = np;
+      h->sorted_pid_ok = pc->pid != nullptr;
+      return MPPIC_OK;
     }
     const int nblk = (int)((np + SORT_TILE - 1) / SORT_TILE);
     const int passes = (h->key_bits + 7) / 8;
@@ -566,7 +605,9 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   const int every = h->cfg.sort_every;
   auto sort_due = [&](long long step) { return every > 0 && step % every == 0; };
   if (!h->order_on_caller || h->order_np != np || sort_due(h->step_counter)) {
-    mppic_status s = sort_into_scratch<T>(h, pc, dst);
+    // the caller's arrays still hold the last step's layout: re-sort locally
+    const bool local = h->order_on_caller && h->order_np == np;
+    mppic_status s = sort_into_scratch<T>(h, pc, dst, false, local);
     if (s) return s;
     src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
   }
@@ -581,7 +622,7 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   for (int it = 0; it < nsteps; ++it) {
     if (it > 0 && sort_due(h->step_counter + it)) {
-      s = sort_into_scratch<T>(h, pc, dst, true);   // keys written by the previous step
+      s = sort_into_scratch<T>(h, pc, dst, true, true);   // keys from the previous step
       if (s) return s;
       src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
     }
@@ -743,7 +784,7 @@ mppic_status bin_impl(mppic_handle* h, mppic_parcels* pc, int do_sort) {
   const long long np = pc->np;
   PArrays<T> cur = caller_arrays<T>(pc);
   if (do_sort) {
-    mppic_status s = sort_into_scratch<T>(h, pc, cur);
+    mppic_status s = sort_into_scratch<T>(h, pc, cur, false, h->order_on_caller && h->order_np == np);
     if (s) return s;
     if (np > 0) {
       for (int f = 0; f < 8; ++f)
@@ -912,7 +953,16 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
       alloc((void**)&h->bstamp, sizeof(int) * (nbricks > 0 ? nbricks : 1)) &&
       alloc((void**)&h->epoch, sizeof(int)) &&
       alloc((void**)&h->obj_slices, sizeof(double) * 3 * OBJ_BLOCKS) &&
-      alloc((void**)&h->obj_count, sizeof(unsigned))) {
+      alloc((void**)&h->obj_count, sizeof(unsigned)) &&
+      alloc((void**)&h->bgeo, sizeof(int4) * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->rs_cnt, sizeof(uint32_t) * NSLOT * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->rs_off, sizeof(uint32_t) * NSLOT * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->rs_wcnt, sizeof(uint32_t) * NSLOT * RS_NW * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->rs_far, sizeof(int) * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->rs_far_next, sizeof(int) * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->rs_count, sizeof(int) * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->rs_start, sizeof(int) * (nbricks > 0 ? nbricks : 1)) &&
+      alloc((void**)&h->rs_part, sizeof(int) * (nbricks / RS_THREADS + 1))) {
     cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(u64) * NQ * h->words * nnode, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->obj_count, 0, sizeof(unsigned), h->stream);
     // no tile slot is valid yet: stamps -1, epoch 0
@@ -922,6 +972,16 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
       std::vector<uint8_t> id((size_t)BCELLS * (nbricks > 0 ? nbricks : 1));
       for (size_t i = 0; i < id.size(); ++i) id[i] = (uint8_t)(i % BCELLS);
       e = cudaMemcpy(h->cellmap, id.data(), id.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && nbricks > 0) {       // brick geometry for the local re-sort
+      std::vector<int4> geo((size_t)nbricks);
+      for (int b = 0; b < nbeds; ++b) {
+        const int nbx = (beds[b].nx + BX - 1) / BX, nby = (beds[b].ny + BY - 1) / BY,
+                  nbz = (beds[b].nz + BZ - 1) / BZ;
+        for (long long g = boff[b]; g < boff[b + 1]; ++g)
+          geo[(size_t)g] = make_int4((int)boff[b], nbx, nby, nbz);
+      }
+      e = cudaMemcpy(h->bgeo, geo.data(), sizeof(int4) * geo.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->errs, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fld, 0, h->tsize * 5 * nnode, h->stream);
@@ -1169,7 +1229,9 @@ void mppic_destroy(mppic_handle* h) {
   cudaFree(h->obj_tmp); cudaFree(h->errs); cudaFree(h->zr); cudaFree(h->totals); cudaFree(h->hist);
   cudaFree(h->obj_slices); cudaFree(h->obj_count); cudaFree(h->cellmap);
   cudaFree(h->bacc); cudaFree(h->bstamp); cudaFree(h->epoch);
-  for (int i = 0; i < 2; ++i) { cudaFree(h->keys[i]); cudaFree(h->vals[i]); }
+  for (int i = 0; i < 2; ++i) { cudaFree(h->keys[i]); cudaFree(h->vals[i]); cudaFree(h->bcell[i]); }
+  cudaFree(h->bgeo); cudaFree(h->rs_cnt); cudaFree(h->rs_off); cudaFree(h->rs_wcnt); cudaFree(h->rs_far);
+  cudaFree(h->rs_far_next); cudaFree(h->rs_count); cudaFree(h->rs_start); cudaFree(h->rs_part);
   for (int f = 0; f < 8; ++f) cudaFree(h->sorted[f]);
   cudaFree(h->sorted_pid);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);

@@ -647,83 +647,185 @@ constexpr unsigned FULL = 0xffffffffu;
 // group the parcels are laid out by level: level r holds the r-th parcel (in sorted order)
 // of every cell of the group that has more than r parcels, in rank order; the warp's r-th
 // iteration then reads one contiguous run.
-// k_level_gather ranks the cells (a bitonic sort in shared memory), records the mapping in
-// cellmap, and permutes the parcel arrays into the layout straight from the sorted order
-// (perm: sorted position -> source index). One CTA per brick.
-template <class T>
-__global__ void __launch_bounds__(BCELLS)
-k_level_gather(PArrays<T> src, PArrays<T> dst, const uint32_t* __restrict__ perm,
-               const int* __restrict__ start, uint8_t* __restrict__ cellmap) {
-  __shared__ uint32_t sk[BCELLS];
-  __shared__ int wa[BCELLS / 32], wb[BCELLS / 32];
-  __shared__ bool s_rank;
-  const long long b = blockIdx.x;
+// level_layout ranks the cells (rank_cells), records the mapping in
+// cellmap, and permutes the parcel arrays into the layout straight from the sorted order.
+// Both sorts end in it: the full radix sort (k_level_gather) and the local re-sort
+// (k_rs_build, in mppic_resort.cuh).
+struct LevelSmem {
+  union {
+    uint32_t sk[BCELLS];         // bitonic ranking keys
+    int hist[8][BCELLS];         // count ranking: per warp, cells of each count
+  };
+  int gt[BCELLS];                // cells with a larger count
+  uint8_t inv[BCELLS];           // cell of each rank
+  int wa[BCELLS / 32], wb[BCELLS / 32];
+  int rank;
+};
+
+// Rank of each cell t by (count descending, index ascending) into ls.inv (cell of rank r).
+// Counts below 256: a count histogram (per warp, so ties keep index order); otherwise a
+// bitonic sort of unique (count, index) keys. Both give the same permutation.
+__device__ __forceinline__ void rank_cells(int cnt, int big, LevelSmem& ls) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const long long k0 = b * BCELLS;
-  const int bs = start[k0], be = start[k0 + BCELLS];
-  const int cnt = start[k0 + t + 1] - start[k0 + t];
+  if (!big) {
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) ls.hist[w][t] = 0;
+    __syncthreads();
+    const unsigned m = __match_any_sync(FULL, cnt);
+    if ((m & below) == 0) ls.hist[warp][cnt] = __popc(m);
+    __syncthreads();
+    // per count c = t: cells in earlier warps (exclusive over warps), and the total
+    int tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const int h = ls.hist[w][t];
+      ls.hist[w][t] = tot;
+      tot += h;
+    }
+    // cells with a count above t: total minus the inclusive scan up to t
+    int inc = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) ls.wa[warp] = inc;
+    __syncthreads();
+    int pre = 0, all = 0;
+    for (int w = 0; w < 8; ++w) {
+      if (w < warp) pre += ls.wa[w];
+      all += ls.wa[w];
+    }
+    ls.gt[t] = all - (pre + inc);
+    __syncthreads();
+    const int r = ls.gt[cnt] + ls.hist[warp][cnt] + __popc(m & below);
+    ls.inv[r] = (uint8_t)t;
+    __syncthreads();
+    return;
+  }
+  ls.sk[t] = ((0xFFFFFFu - (uint32_t)min(cnt, 0xFFFFFF)) << 8) | (uint32_t)t;
+  __syncthreads();
+  for (int k = 2; k <= BCELLS; k <<= 1) {        // ascending bitonic sort of unique keys
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int ixj = t ^ j;
+      if (ixj > t) {
+        const uint32_t a = ls.sk[t], c = ls.sk[ixj];
+        if ((a > c) == ((t & k) == 0)) { ls.sk[t] = c; ls.sk[ixj] = a; }
+      }
+      __syncthreads();
+    }
+  }
+  ls.inv[t] = (uint8_t)(ls.sk[t] & 255u);
+  __syncthreads();
+}
+
+// One CTA (BCELLS threads) lays out brick k0 / BCELLS: its parcels occupy sorted positions
+// [bs, bs + cs[BCELLS]); cs (shared) holds each cell's first position relative to bs, and
+// perm[i] the source index of relative sorted position i (shared or global).
+template <class T>
+__device__ __forceinline__ void level_layout(const PArrays<T>& src, const PArrays<T>& dst,
+                                             long long k0, int bs, const int* cs,
+                                             const uint32_t* perm, uint8_t* __restrict__ cellmap,
+                                             LevelSmem& ls) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (cs[BCELLS] == 0) {                         // an empty brick: own order (never ranked)
+    cellmap[k0 + t] = (uint8_t)t;
+    return;
+  }
+  const int cnt = cs[t + 1] - cs[t];
   // even counts (no empty cell, the largest at most 1.5 x the smallest): ranking cannot
   // save a quarter of the warp iterations, and is skipped
   {
     const int mn = __reduce_min_sync(FULL, cnt), mx = __reduce_max_sync(FULL, cnt);
-    if (lane == 0) { wa[warp] = mn; wb[warp] = mx; }
+    if (lane == 0) { ls.wa[warp] = mn; ls.wb[warp] = mx; }
     __syncthreads();
     if (t == 0) {
-      int bmn = wa[0], bmx = wb[0];
-      for (int w = 1; w < BCELLS / 32; ++w) { bmn = min(bmn, wa[w]); bmx = max(bmx, wb[w]); }
-      s_rank = !(bmn > 0 && 2 * bmx <= 3 * bmn);
+      int bmn = ls.wa[0], bmx = ls.wb[0];
+      for (int w = 1; w < BCELLS / 32; ++w) { bmn = min(bmn, ls.wa[w]); bmx = max(bmx, ls.wb[w]); }
+      ls.rank = bmn > 0 && 2 * bmx <= 3 * bmn ? 0 : (bmx < BCELLS ? 1 : 2);
     }
     __syncthreads();
   }
   int cell = t;
-  if (s_rank) {                                  // uniform over the CTA
-    sk[t] = ((0xFFFFFFu - (uint32_t)min(cnt, 0xFFFFFF)) << 8) | (uint32_t)t;
-    __syncthreads();
-    for (int k = 2; k <= BCELLS; k <<= 1) {      // ascending bitonic sort of unique keys
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        const int ixj = t ^ j;
-        if (ixj > t) {
-          const uint32_t a = sk[t], c = sk[ixj];
-          if ((a > c) == ((t & k) == 0)) { sk[t] = c; sk[ixj] = a; }
-        }
-        __syncthreads();
-      }
-    }
+  if (ls.rank) {                                 // uniform over the CTA
+    const int mode = ls.rank;
+    __syncthreads();                             // wa is rewritten by the ranking
+    rank_cells(cnt, mode == 2, ls);
     // ranked only if it saves more than a quarter of the warp iterations (the sum over
     // warps of the warp's largest count)
-    const int rc = (int)(0xFFFFFFu - (sk[t] >> 8));  // count of the cell of rank t
+    const int ct = ls.inv[t];
+    const int rc = cs[ct + 1] - cs[ct];          // count of the cell of rank t
     const int m_own = __reduce_max_sync(FULL, cnt), m_rank = __reduce_max_sync(FULL, rc);
-    if (lane == 0) { wa[warp] = m_own; wb[warp] = m_rank; }
+    if (lane == 0) { ls.wa[warp] = m_own; ls.wb[warp] = m_rank; }
     __syncthreads();
     int sum_own = 0, sum_rank = 0;
-    for (int w = 0; w < BCELLS / 32; ++w) { sum_own += wa[w]; sum_rank += wb[w]; }
-    if (4 * sum_rank < 3 * sum_own) cell = (int)(sk[t] & 255u);
+    for (int w = 0; w < BCELLS / 32; ++w) { sum_own += ls.wa[w]; sum_rank += ls.wb[w]; }
+    if (4 * sum_rank < 3 * sum_own) cell = ct;
     __syncthreads();                             // wa is reused below
   }
   cellmap[k0 + t] = (uint8_t)cell;
-  if (bs == be) return;                          // the whole CTA: an empty brick
-  const int cs = start[k0 + cell];
-  const int n = start[k0 + cell + 1] - cs;
+  const int c0 = cs[cell];
+  const int n = cs[cell + 1] - c0;
   const int ws = __reduce_add_sync(FULL, n);
-  if (lane == 0) wa[warp] = ws;
+  if (lane == 0) ls.wa[warp] = ws;
   __syncthreads();
   int off = bs;                                  // first parcel of this warp's group
-  for (int w = 0; w < warp; ++w) off += wa[w];
+  for (int w = 0; w < warp; ++w) off += ls.wa[w];
   const int nmax = __reduce_max_sync(FULL, n);
   const unsigned below = (1u << lane) - 1u;
-  for (int r = 0; r < nmax; ++r) {
-    const bool act = n > r;
-    const unsigned bal = __ballot_sync(FULL, act);
-    if (act) {
-      const int q = off + __popc(bal & below);
-      const uint32_t s = perm[cs + r];
+  // two levels per iteration, all loads before the stores
+  for (int r = 0; r < nmax; r += 2) {
+    const bool a0 = n > r, a1 = n > r + 1;
+    const unsigned b0 = __ballot_sync(FULL, a0), b1 = __ballot_sync(FULL, a1);
+    const int q0 = off + __popc(b0 & below);
+    const int q1 = off + __popc(b0) + __popc(b1 & below);
+    const uint32_t s0 = a0 ? perm[c0 + r] : 0u;
+    const uint32_t s1 = a1 ? perm[c0 + r + 1] : 0u;
+    T v0[8], v1[8];
+    int i0 = 0, i1 = 0, g0 = 0, g1 = 0;
+    if (a0) {
 #pragma unroll
-      for (int f = 0; f < 8; ++f) dst.a[f][q] = src.a[f][s];
-      if (src.pid) dst.pid[q] = src.pid[s];
-      if (src.tag) dst.tag[q] = src.tag[s];
+      for (int f = 0; f < 8; ++f) v0[f] = __ldg(src.a[f] + s0);
+      if (src.pid) i0 = __ldg(src.pid + s0);
+      if (src.tag) g0 = __ldg(src.tag + s0);
     }
-    off += __popc(bal);
+    if (a1) {
+#pragma unroll
+      for (int f = 0; f < 8; ++f) v1[f] = __ldg(src.a[f] + s1);
+      if (src.pid) i1 = __ldg(src.pid + s1);
+      if (src.tag) g1 = __ldg(src.tag + s1);
+    }
+    if (a0) {
+#pragma unroll
+      for (int f = 0; f < 8; ++f) dst.a[f][q0] = v0[f];
+      if (src.pid) dst.pid[q0] = i0;
+      if (src.tag) dst.tag[q0] = g0;
+    }
+    if (a1) {
+#pragma unroll
+      for (int f = 0; f < 8; ++f) dst.a[f][q1] = v1[f];
+      if (src.pid) dst.pid[q1] = i1;
+      if (src.tag) dst.tag[q1] = g1;
+    }
+    off += __popc(b0) + __popc(b1);
   }
+}
+
+// The level layout after the full radix sort: perm maps each sorted position to its source
+// index, start each key to its first sorted position. One CTA per brick.
+template <class T>
+__global__ void __launch_bounds__(BCELLS)
+k_level_gather(PArrays<T> src, PArrays<T> dst, const uint32_t* __restrict__ perm,
+               const int* __restrict__ start, uint8_t* __restrict__ cellmap) {
+  __shared__ int s_cs[BCELLS + 1];
+  __shared__ LevelSmem ls;
+  const long long k0 = (long long)blockIdx.x * BCELLS;
+  const int t = threadIdx.x;
+  const int bs = start[k0];
+  s_cs[t] = start[k0 + t] - bs;
+  if (t == 0) s_cs[BCELLS] = start[k0 + BCELLS] - bs;
+  __syncthreads();
+  level_layout<T>(src, dst, k0, bs, s_cs, perm + bs, cellmap, ls);
 }
 
 // ---- math of the step: full precision in the FP64 form, CUDA's fast intrinsics in FP32.

@@ -88,26 +88,18 @@ def test_binning_bit_exact_including_faces(prec):
     assert np.array_equal(dev["cell"].cpu().numpy(), cell_ref)
 
 
-@pytest.mark.parametrize("prec", [32, 64])
-def test_sort_is_a_stable_level_permutation(prec):
-    """After a sort, each brick's 256 cells are taken 32 at a time, either in their own order
-    or ranked by parcel count (descending, ties by cell index), the latter where it cuts the
-    sum over groups of the group's largest count by more than a quarter (not tried where no
-    cell is empty and the largest count is at most 1.5 times the smallest); the parcels of
-    each group are stored level by level: the r-th parcel of every cell of the group that
-    has one, in group order, then level r+1; within a cell parcels keep their original
-    order."""
-    bed = synth.settle_bed(n=50_000, nx=20, ny=12, nz=9)   # grid not a multiple of the brick
-    b = mppic.Bed(bed.params, precision=prec)
-    dev = mppic.parcels_to_device(bed.parcels, prec, with_pid=True)
-    x0 = host(dev["x"]).copy()
-    b.bin(dev, do_sort=True)
-    pid = dev["pid"].cpu().numpy()
-    assert np.array_equal(np.sort(pid), np.arange(bed.np))
-    np.testing.assert_array_equal(host(dev["x"]), x0[pid])        # arrays moved together
-    cell = dev["cell"].cpu().numpy()
-    i, j, k = cell % 20, (cell // 20) % 12, cell // 240
-    nbx, nby, nbz = 3, 2, 3
+def check_level_layout(cell, orig, nx, ny, nz):
+    """The layout rule of a sort: each brick's 256 cells are taken 32 at a time, either in
+    their own order or ranked by parcel count (descending, ties by cell index), the latter
+    where it cuts the sum over groups of the group's largest count by more than a quarter
+    (not tried where no cell is empty and the largest count is at most 1.5 times the
+    smallest); the parcels of each group are stored level by level: the r-th parcel of every
+    cell of the group that has one, in group order, then level r+1; within a cell parcels
+    keep their order before the sort (`orig`: each parcel's index before it). Returns which
+    bricks were ranked."""
+    n = cell.size
+    i, j, k = cell % nx, (cell // nx) % ny, cell // (nx * ny)
+    nbx, nby, nbz = -(-nx // 8), -(-ny // 8), -(-nz // 4)
     brick = (i // 8) + nbx * ((j // 8) + nby * (k // 4))
     local = (i % 8) + 8 * ((j % 8) + 8 * (k % 4))
     key = brick * 256 + local
@@ -122,13 +114,12 @@ def test_sort_is_a_stable_level_permutation(prec):
     even = (counts.min(axis=1) > 0) & (2 * counts.max(axis=1) <= 3 * counts.min(axis=1))
     ranked = ~even & (4 * it_rank < 3 * it_own)
     rank = np.where(ranked[:, None], rank, idx)
-    assert ranked.any() and not ranked.all()       # the bed exercises both choices
     rk = rank[brick, local]
-    # rank of each parcel within its cell, in original order (a stable sort keeps that order)
-    o = np.lexsort((pid, key))
+    # rank of each parcel within its cell, in the order before the sort
+    o = np.lexsort((orig, key))
     first = np.searchsorted(key[o], key[o], side="left")
-    lvl = np.empty_like(pid)
-    lvl[o] = np.arange(bed.np) - first
+    lvl = np.empty(n, np.int64)
+    lvl[o] = np.arange(n) - first
     t = np.stack([brick, rk // 32, lvl, rk], axis=1)
     d = np.diff(t, axis=0)
     inc = np.zeros(len(d), bool)
@@ -137,6 +128,109 @@ def test_sort_is_a_stable_level_permutation(prec):
         inc |= eq & (d[:, c] > 0)
         eq &= d[:, c] == 0
     assert np.all(inc)
+    return ranked
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_sort_is_a_stable_level_permutation(prec):
+    bed = synth.settle_bed(n=50_000, nx=20, ny=12, nz=9)   # grid not a multiple of the brick
+    b = mppic.Bed(bed.params, precision=prec)
+    dev = mppic.parcels_to_device(bed.parcels, prec, with_pid=True)
+    x0 = host(dev["x"]).copy()
+    b.bin(dev, do_sort=True)
+    pid = dev["pid"].cpu().numpy()
+    assert np.array_equal(np.sort(pid), np.arange(bed.np))
+    np.testing.assert_array_equal(host(dev["x"]), x0[pid])        # arrays moved together
+    ranked = check_level_layout(dev["cell"].cpu().numpy(), pid, 20, 12, 9)
+    assert ranked.any() and not ranked.all()       # the bed exercises both choices
+
+
+FIELDS = ("x", "y", "z", "u", "v", "w", "d", "omega", "pid")
+
+
+def _move(dev, params, moves, seed):
+    """Move the parcels on the device: 'near' by up to 0.4 cell per axis; 'far' the same plus
+    5% of the parcels anywhere in the box; 'shuffled' a random permutation of the arrays."""
+    rng = np.random.default_rng(seed)
+    n = dev["x"].numel()
+    if moves == "shuffled":
+        perm = torch.from_numpy(rng.permutation(n)).to(dev["x"].device)
+        for f in FIELDS:
+            dev[f].copy_(dev[f][perm])
+        return
+    h = np.array([params["dx"], params["dy"], params["dz"]])
+    L = h * np.array([params["nx"], params["ny"], params["nz"]])
+    pos = np.stack([host(dev[a]) for a in "xyz"], axis=1)
+    pos += rng.uniform(-0.4, 0.4, (n, 3)) * h
+    if moves == "far":
+        sel = rng.random(n) < 0.05
+        pos[sel] = rng.uniform(0.0, 1.0, (int(sel.sum()), 3)) * L
+    pos = np.clip(pos, 0.0, L * (1 - 1e-6))
+    for a, c in enumerate("xyz"):
+        dev[c].copy_(torch.from_numpy(pos[:, a]).to(dev[c].dtype))
+
+
+def _copy(dev):
+    return {k: v.clone() for k, v in dev.items()}
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("moves", ["near", "far", "shuffled"])
+@pytest.mark.parametrize("grid", [(50_000, 20, 12, 9), (20_000, 8, 8, 4), (60_000, 24, 8, 4)])
+def test_local_resort_equals_full_sort(prec, moves, grid):
+    """A sort that starts from the previous sort's layout re-sorts each brick from its own
+    range and its 26 neighbours' (mppic_resort.cuh). Its result must be exactly the full
+    radix sort's (a fresh handle, same input order): for parcels that stayed near, for
+    parcels that moved anywhere ('far'), for an order unrelated to the layout ('shuffled'),
+    and for bricks whose parcels exceed the shared-memory permutation (the 1-brick grid; the
+    3-brick row, where shuffling also sends parcels beyond the neighbours)."""
+    n, nx, ny, nz = grid
+    bed = synth.settle_bed(n=n, nx=nx, ny=ny, nz=nz, seed=41)
+    b = mppic.Bed(bed.params, precision=prec)
+    dev = mppic.parcels_to_device(bed.parcels, prec, with_pid=True)
+    b.bin(dev, do_sort=True)                       # first sort: the full radix sort
+    _move(dev, bed.params, moves, seed=5)
+    before = _copy(dev)
+    b.bin(dev, do_sort=True)                       # second sort: local
+    b.check()
+    fresh = mppic.Bed(bed.params, precision=prec)
+    full = _copy(before)
+    fresh.bin(full, do_sort=True)
+    fresh.check()
+    for f in FIELDS + ("cell",):
+        assert torch.equal(dev[f], full[f]), f
+    pre = before["pid"].cpu().numpy()
+    inv = np.empty_like(pre)
+    inv[pre] = np.arange(n)
+    orig = inv[dev["pid"].cpu().numpy()]
+    np.testing.assert_array_equal(host(dev["x"]), host(before["x"])[orig])
+    check_level_layout(dev["cell"].cpu().numpy(), orig, nx, ny, nz)
+
+
+@pytest.mark.parametrize("moves", ["near", "far"])
+def test_local_resort_batch_equals_full_sort(moves):
+    """The same for a batch: brick neighbours never cross beds."""
+    beds = [synth.settle_bed(n=n, nx=g[0], ny=g[1], nz=g[2], seed=60 + k)
+            for k, (g, n) in enumerate((((9, 8, 16), 3000), ((16, 16, 20), 9000), ((8, 8, 4), 0),
+                                        ((20, 7, 33), 12000)))]
+    batch = mppic.Batch([b.params for b in beds], [b.np for b in beds], precision=32)
+    dev, _ = mppic.concat_beds(beds, 32, with_pid=True)
+    batch.bin(dev, do_sort=True)
+    off = batch.offsets
+    for k, bd in enumerate(beds):                  # move each bed's parcels in its own box
+        if bd.np == 0:
+            continue
+        part = {f: dev[f][off[k]:off[k + 1]] for f in FIELDS}
+        _move(part, bd.params, moves, seed=70 + k)
+    before = _copy(dev)
+    batch.bin(dev, do_sort=True)
+    batch.check()
+    fresh = mppic.Batch([b.params for b in beds], [b.np for b in beds], precision=32)
+    full = _copy(before)
+    fresh.bin(full, do_sort=True)
+    fresh.check()
+    for f in FIELDS + ("cell",):
+        assert torch.equal(dev[f], full[f]), f
 
 
 # --------------------------------------------------------------- deposit --
