@@ -360,10 +360,25 @@ __global__ void k_keys(KParams<T> p, const T* __restrict__ x, const T* __restric
   key[q] = brick_key(p, c.i, c.j, c.k);
 }
 
+// The lanes of the warp whose v equals this lane's (what __match_any_sync(FULL, v) returns),
+// from one ballot per bit of v, 0 <= v < 2^BITS. All 32 lanes must call it. Ballots run at
+// full rate; a warp-wide match over up to 32 distinct values does not.
+template <int BITS>
+__device__ __forceinline__ unsigned match_bits(unsigned v) {
+  unsigned m = 0xffffffffu;
+#pragma unroll
+  for (int i = 0; i < BITS; ++i) {
+    const bool bit = (v >> i) & 1u;
+    const unsigned bl = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bl : ~bl;
+  }
+  return m;
+}
+
 // ------------------------------------------------------------ radix sort --
 // Stable LSD radix sort of (key, value) by 8-bit digits: a per-tile digit histogram, a
 // scan per digit across tiles, then a stable scatter in which each warp ranks its own
-// contiguous segment with __match_any_sync.
+// contiguous segment with match_bits.
 
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_TILE = 4096;
@@ -410,7 +425,7 @@ __global__ void k_sort_scan(uint32_t* __restrict__ hist, int nblk, uint32_t* __r
 }
 
 // Two forms of the stable scatter of one digit pass. Both rank each warp's segment with
-// __match_any_sync. k_sort_scatter_direct writes every key straight to its output
+// match_bits. k_sort_scatter_direct writes every key straight to its output
 // position: best when a tile's keys mostly share a digit (the upper digits of nearly
 // sorted keys). k_sort_scatter_reorder first places the tile in digit order in shared
 // memory and writes it out in that order, so each digit's run lands on consecutive
@@ -446,11 +461,9 @@ k_sort_scatter_direct(const uint32_t* __restrict__ kin, const uint32_t* __restri
     bool ok = q < n;
     unsigned act = __ballot_sync(0xffffffffu, ok);
     if (!act) break;
-    if (ok) {
-      uint32_t d = (kin[q] >> shift) & 255u;
-      unsigned m = __match_any_sync(act, d);
-      if ((m & lt) == 0) wcnt[warp][d] += __popc(m);
-    }
+    const uint32_t d = ok ? (kin[q] >> shift) & 255u : 0u;
+    const unsigned m = match_bits<8>(d) & act;
+    if (ok && (m & lt) == 0) wcnt[warp][d] += __popc(m);
     __syncwarp();
   }
   __syncthreads();
@@ -469,15 +482,11 @@ k_sort_scatter_direct(const uint32_t* __restrict__ kin, const uint32_t* __restri
     bool ok = q < n;
     unsigned act = __ballot_sync(0xffffffffu, ok);
     if (!act) break;
-    uint32_t k = 0, d = 0;
-    unsigned m = 0;
+    const uint32_t k = ok ? kin[q] : 0u;
+    const uint32_t d = (k >> shift) & 255u;
+    const unsigned m = match_bits<8>(d) & act;
     uint32_t pos = 0;
-    if (ok) {
-      k = kin[q];
-      d = (k >> shift) & 255u;
-      m = __match_any_sync(act, d);
-      pos = wcnt[warp][d] + __popc(m & lt);
-    }
+    if (ok) pos = wcnt[warp][d] + __popc(m & lt);
     __syncwarp();
     if (ok) {
       kout[pos] = k;
@@ -522,11 +531,9 @@ k_sort_scatter_reorder(const uint32_t* __restrict__ kin, const uint32_t* __restr
     const bool ok = r < tn;
     const unsigned act = __ballot_sync(0xffffffffu, ok);
     if (!act) break;
-    if (ok) {
-      const uint32_t d = (kin[tbase + r] >> shift) & 255u;
-      const unsigned m = __match_any_sync(act, d);
-      if ((m & lt) == 0) wcnt[warp][d] += __popc(m);
-    }
+    const uint32_t d = ok ? (kin[tbase + r] >> shift) & 255u : 0u;
+    const unsigned m = match_bits<8>(d) & act;
+    if (ok && (m & lt) == 0) wcnt[warp][d] += __popc(m);
     __syncwarp();
   }
   __syncthreads();
@@ -559,12 +566,10 @@ k_sort_scatter_reorder(const uint32_t* __restrict__ kin, const uint32_t* __restr
     const bool ok = r < tn;
     const unsigned act = __ballot_sync(0xffffffffu, ok);
     if (!act) break;
-    uint32_t d = 0;
-    unsigned m = 0;
+    const uint32_t k = ok ? kin[tbase + r] : 0u;
+    const uint32_t d = (k >> shift) & 255u;
+    const unsigned m = match_bits<8>(d) & act;
     if (ok) {
-      const uint32_t k = kin[tbase + r];
-      d = (k >> shift) & 255u;
-      m = __match_any_sync(act, d);
       const uint32_t loc = lbase[d] + wcnt[warp][d] + __popc(m & lt);
       sk[loc] = k;
       sv[loc] = vin ? vin[tbase + r] : (uint32_t)(tbase + r);
@@ -672,7 +677,7 @@ __device__ __forceinline__ void rank_cells(int cnt, int big, LevelSmem& ls) {
 #pragma unroll
     for (int w = 0; w < 8; ++w) ls.hist[w][t] = 0;
     __syncthreads();
-    const unsigned m = __match_any_sync(FULL, cnt);
+    const unsigned m = match_bits<8>((unsigned)cnt);
     if ((m & below) == 0) ls.hist[warp][cnt] = __popc(m);
     __syncthreads();
     // per count c = t: cells in earlier warps (exclusive over warps), and the total
@@ -773,41 +778,42 @@ __device__ __forceinline__ void level_layout(const PArrays<T>& src, const PArray
   for (int w = 0; w < warp; ++w) off += ls.wa[w];
   const int nmax = __reduce_max_sync(FULL, n);
   const unsigned below = (1u << lane) - 1u;
-  // two levels per iteration, all loads before the stores
-  for (int r = 0; r < nmax; r += 2) {
-    const bool a0 = n > r, a1 = n > r + 1;
-    const unsigned b0 = __ballot_sync(FULL, a0), b1 = __ballot_sync(FULL, a1);
-    const int q0 = off + __popc(b0 & below);
-    const int q1 = off + __popc(b0) + __popc(b1 & below);
-    const uint32_t s0 = a0 ? perm[c0 + r] : 0u;
-    const uint32_t s1 = a1 ? perm[c0 + r + 1] : 0u;
-    T v0[8], v1[8];
-    int i0 = 0, i1 = 0, g0 = 0, g1 = 0;
-    if (a0) {
+  // L levels per iteration (4 FP32, 2 FP64), all loads before the stores
+  constexpr int L = sizeof(T) == 4 ? 4 : 2;
+  for (int r = 0; r < nmax; r += L) {
+    bool a[L];
+    int q[L];
+    uint32_t si[L];
+    int acc = off;
 #pragma unroll
-      for (int f = 0; f < 8; ++f) v0[f] = __ldg(src.a[f] + s0);
-      if (src.pid) i0 = __ldg(src.pid + s0);
-      if (src.tag) g0 = __ldg(src.tag + s0);
+    for (int l = 0; l < L; ++l) {
+      a[l] = n > r + l;
+      const unsigned bl = __ballot_sync(FULL, a[l]);
+      q[l] = acc + __popc(bl & below);
+      acc += __popc(bl);
+      si[l] = a[l] ? perm[c0 + r + l] : 0u;
     }
-    if (a1) {
+    T v[L][8];
+    int ip[L], ig[L];
 #pragma unroll
-      for (int f = 0; f < 8; ++f) v1[f] = __ldg(src.a[f] + s1);
-      if (src.pid) i1 = __ldg(src.pid + s1);
-      if (src.tag) g1 = __ldg(src.tag + s1);
-    }
-    if (a0) {
+    for (int l = 0; l < L; ++l) {
+      if (a[l]) {
 #pragma unroll
-      for (int f = 0; f < 8; ++f) dst.a[f][q0] = v0[f];
-      if (src.pid) dst.pid[q0] = i0;
-      if (src.tag) dst.tag[q0] = g0;
+        for (int f = 0; f < 8; ++f) v[l][f] = __ldg(src.a[f] + si[l]);
+        if (src.pid) ip[l] = __ldg(src.pid + si[l]);
+        if (src.tag) ig[l] = __ldg(src.tag + si[l]);
+      }
     }
-    if (a1) {
 #pragma unroll
-      for (int f = 0; f < 8; ++f) dst.a[f][q1] = v1[f];
-      if (src.pid) dst.pid[q1] = i1;
-      if (src.tag) dst.tag[q1] = g1;
+    for (int l = 0; l < L; ++l) {
+      if (a[l]) {
+#pragma unroll
+        for (int f = 0; f < 8; ++f) dst.a[f][q[l]] = v[l][f];
+        if (src.pid) dst.pid[q[l]] = ip[l];
+        if (src.tag) dst.tag[q[l]] = ig[l];
+      }
     }
-    off += __popc(b0) + __popc(b1);
+    off = acc;
   }
 }
 

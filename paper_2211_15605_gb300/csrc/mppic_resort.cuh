@@ -28,7 +28,7 @@ namespace mppic {
 
 constexpr int NSLOT = 27;          // neighbour slots (dx+1) + 3 (dy+1) + 9 (dz+1)
 constexpr int RS_THREADS = 256;
-constexpr int RS_CAP = 6144;       // bucket size up to which the permutation stays in shared memory
+constexpr int RS_CAP = 4096;       // bucket size up to which the brick sorts in shared memory
 
 // Brick geometry: {first brick of the bed, bricks along x, y, z}, one entry per brick.
 __device__ __forceinline__ void rs_coords(int4 g, long long b, int& x, int& y, int& z) {
@@ -125,7 +125,7 @@ k_rs_hist(const uint32_t* __restrict__ key, const int* __restrict__ cstart,
         const bool ok = i0 + j * 32 + lane < hi;
         const uint32_t B = kk[j] / BCELLS;
         const int slot = !ok ? -2 : (B == (uint32_t)b ? 13 : rs_slot(g, bx, by, bz, B));
-        const unsigned m = __match_any_sync(FULL, slot);
+        const unsigned m = match_bits<5>((unsigned)(slot + 2));
         if (slot >= 0) {
           if ((m & below) == 0) s_w[warp][slot] += __popc(m);
         } else if (slot == -1) {
@@ -244,7 +244,7 @@ k_rs_scatter(const uint32_t* __restrict__ key, const int* __restrict__ cstart,
         const bool ok = q < hi;
         const uint32_t B = kk[j] / BCELLS;
         const int slot = !ok ? -2 : (B == (uint32_t)b ? 13 : rs_slot(g, bx, by, bz, B));
-        const unsigned m = __match_any_sync(FULL, slot);
+        const unsigned m = match_bits<5>((unsigned)(slot + 2));
         if (slot >= -1) {
           const int pos = slot >= 0 ? s_w[warp][slot] + __popc(m & below) : atomicAdd(&far_next[B], 1);
           bsrc[pos] = (uint32_t)q;
@@ -262,7 +262,7 @@ k_rs_scatter(const uint32_t* __restrict__ key, const int* __restrict__ cstart,
 // One stable counting pass over n (source index, cell byte) pairs by a 256-way digit, by
 // the whole CTA. Warp w takes a contiguous segment: it counts its pairs per digit; a prefix
 // over digits and warps gives each warp's first position per digit; the warp then places
-// its pairs in order, ranked within each 32 by __match_any_sync.
+// its pairs in order, ranked within each 32 by match_bits.
 struct RsPass {
   int w[RS_NW][256];             // per warp and digit: count, then next position
   int start[256];                // digit starts
@@ -299,7 +299,7 @@ __device__ void rs_pass(const uint32_t* in_s, const uint8_t* in_c, uint32_t* out
     }
 #pragma unroll
     for (int j = 0; j < RS_U; ++j) {
-      const unsigned m = __match_any_sync(FULL, dd[j]);
+      const unsigned m = match_bits<8>((unsigned)dd[j] & 255u) & __ballot_sync(FULL, dd[j] >= 0);
       if (dd[j] >= 0 && (m & below) == 0) ps.w[warp][dd[j]] += __popc(m);
       __syncwarp();
     }
@@ -331,8 +331,10 @@ __device__ void rs_pass(const uint32_t* in_s, const uint8_t* in_c, uint32_t* out
 #pragma unroll
     for (int j = 0; j < RS_U; ++j) {
       const bool ok = i0 + j * 32 + lane < hi;
-      const int d = ok ? dig(ss[j], cc[j]) : -1;
-      const unsigned m = __match_any_sync(FULL, d);
+      const int d = ok ? dig(ss[j], cc[j]) : 0;
+      // the lanes' digits are usually distinct (consecutive pairs of a level layout are
+      // different cells): then each lane takes the digit's next position alone
+      const unsigned m = match_bits<8>((unsigned)d) & __ballot_sync(FULL, ok);
       if (ok) {
         const int pos = ps.w[warp][d] + __popc(m & below);
         out_s[pos] = ss[j];
@@ -347,8 +349,8 @@ __device__ void rs_pass(const uint32_t* in_s, const uint8_t* in_c, uint32_t* out
 }
 
 template <class T> struct RsOccupancy;
-template <> struct RsOccupancy<float> { static constexpr int ctas = 6; };
-template <> struct RsOccupancy<double> { static constexpr int ctas = 5; };
+template <> struct RsOccupancy<float> { static constexpr int ctas = 4; };
+template <> struct RsOccupancy<double> { static constexpr int ctas = 4; };
 
 template <class T>
 __global__ void __launch_bounds__(RS_THREADS, RsOccupancy<T>::ctas)
@@ -361,6 +363,8 @@ k_rs_build(PArrays<T> src, PArrays<T> dst, const int* __restrict__ bstart,
     LevelSmem ls;
   } u;
   __shared__ uint32_t s_perm[RS_CAP];
+  __shared__ uint32_t s_src[RS_CAP];
+  __shared__ uint8_t s_cell[RS_CAP];
   __shared__ int s_cs[BCELLS + 1];
   __shared__ uint32_t s_mn[RS_NW], s_mx[RS_NW];
   const long long B = blockIdx.x, k0 = B * BCELLS;
@@ -397,7 +401,30 @@ k_rs_build(PArrays<T> src, PArrays<T> dst, const int* __restrict__ bstart,
       uint8_t* tc = ic; ic = oc; oc = tc;
     }
   }
-  uint32_t* perm = n <= RS_CAP ? s_perm : os;    // os: the buffer not holding the input
+  uint32_t* perm = os;                           // os: the buffer not holding the input
+  if (n <= RS_CAP) {             // the whole bucket into shared memory, all loads in flight
+    constexpr int PER = RS_CAP / RS_THREADS;
+    uint32_t vs[PER];
+    uint8_t vc[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = j * RS_THREADS + t;
+      vs[j] = i < n ? is[i] : 0u;
+      vc[j] = i < n ? ic[i] : (uint8_t)0;
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = j * RS_THREADS + t;
+      if (i < n) {
+        s_src[i] = vs[j];
+        s_cell[i] = vc[j];
+      }
+    }
+    __syncthreads();
+    is = s_src;
+    ic = s_cell;
+    perm = s_perm;
+  }
   rs_pass(is, ic, perm, nullptr, n, DigitOfCell{}, u.ps);
   const int cs = u.ps.start[t];
   __syncthreads();                               // u.ps is reused as u.ls
