@@ -3,18 +3,24 @@
 
 A "step" is one pass of the whole hot path over the bed: deposit of the solids volume,
 node fields, interpolation, Wen-Yu drag, stress gradient, drag-sum deposit, push with wall
-reflection, re-binning, objectives, and the sort by cell every --sort-every steps. The
-default workload is the dense bed: 128x128x512 cells of 1 cm, 32M parcels filling the
-bottom quarter at solids fraction 0.5 (lognormal d, median 100 um, sigma 0.4), inflow
-0.8 m/s, FP32 state with exact fixed-point deposits, sorted every 10 steps.
+reflection, re-binning, objectives, and the sort by cell every --sort-every steps (default
+every step). The default workload is the dense bed: 128x128x512 cells of 1 cm, 32M parcels
+filling the bottom quarter at solids fraction 0.5 (lognormal d, median 100 um, sigma 0.4),
+inflow 0.8 m/s, FP32 state with exact fixed-point deposits, run for 500 steps.
+
+The bed fluidises over the run and a step gets slower as it does, so the timed window is
+centred in the run: with the default 500 timed steps it is the whole run (after the
+warm-up); a shorter --steps is preceded by untimed settling steps. config.timed_steps
+states the window.
 
 Prints one JSON line. `value` is whole-job parcel-updates/s with inputs resident in HBM
 (CUDA events on the library's stream around exactly --steps steps). `e2e` is the same
 metric through the C ABI with the parcel state copied from pinned host memory before and
 back after every step. `roofline` is the fused step kernel's algorithmic bytes per launch
 over its event-timed duration against the measured HBM copy bandwidth. `cpu_baseline` is
-the FP64 CPU oracle on a bounded sample of the same bed. `sort_every_step` times the same bed
-sorted by cell every step (the other schedule of this workload); `fp64_form` the FP64 form;
+the FP64 CPU oracle on a bounded sample of the same bed. `alt_schedule` times the same bed
+over the same window sorted every --alt-sort-every steps (the other schedule of this
+workload, on a fresh handle); `fp64_form` the FP64 form;
 `adjoint` the forward (with checkpoints) and reverse sweeps on the 500k-parcel
 differentiation bed.
 
@@ -43,25 +49,40 @@ UNIT = "parcel-updates/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the workload's whole run)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--run-steps", type=int, default=None,
+                    help="length of the workload's run (default: its own); the timed window is "
+                         "centred in it")
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--workload", choices=("dense", "fourier", "settle", "grad", "batched"),
                     default="dense")
     ap.add_argument("--nbeds", type=int, default=256, help="beds of the batched workload")
     ap.add_argument("--np", type=int, default=None, help="override the parcel count")
     ap.add_argument("--grid", type=str, default=None, help="override the grid, e.g. 64,64,256")
-    ap.add_argument("--sort-every", type=int, default=10)
+    ap.add_argument("--sort-every", type=int, default=1)
+    ap.add_argument("--alt-sort-every", type=int, default=10,
+                    help="the other sort schedule, timed over the same window (0 = skip)")
     ap.add_argument("--precision", type=int, choices=(32, 64), default=32)
     ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64-form comparison (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--adjoint-steps", type=int, default=200,
                     help="steps of the reverse-mode timing on the differentiation bed (0 = skip)")
-    ap.add_argument("--sort1-steps", type=int, default=5,
-                    help="steps of the sort-every-step measurement (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="parcels in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="budget of the reference arm's timed oracle steps")
+    args = ap.parse_args()
+    if args.run_steps is None:
+        args.run_steps = RUN_STEPS[args.workload]
+    if args.steps is None:
+        args.steps = args.run_steps
+    return args
+
+
+# length of each workload's run (the configurations' step counts)
+RUN_STEPS = {"dense": 500, "fourier": 1000, "settle": 100, "grad": 200, "batched": 200}
 
 
 def make_workload(name, np_override=None, seed_offset=0, grid=None):
@@ -82,10 +103,17 @@ def make_workload(name, np_override=None, seed_offset=0, grid=None):
     return bed
 
 
+def settle_steps(args):
+    """Untimed steps before the warm-up that centre the timed window in the run."""
+    return max(0, (args.run_steps - args.steps) // 2 - args.warmup)
+
+
 def workload_config(bed, args):
     p = bed.params
+    t0 = settle_steps(args) + args.warmup
     return {"workload": bed.meta["workload"], "parcels": bed.np,
             "grid": [p["nx"], p["ny"], p["nz"]], "cell_m": p["dx"], "sort_every": args.sort_every,
+            "run_steps": args.run_steps, "timed_steps": [t0, t0 + args.steps],
             "state": "fp32" if args.precision == 32 else "fp64",
             "deposit": "exact fixed point (int64)" if args.precision == 32 else "exact fixed point (int128)",
             "l2": "inputs larger than L2 (parcel state %.2f GB)" % (bed.np * (36 if args.precision == 32 else 68) / 1e9)}
@@ -208,12 +236,12 @@ def run_gpu(args):
     b = mppic.Bed(bed.params, precision=args.precision, sort_every=args.sort_every, stream=stream)
     parcels = mppic.parcels_to_device(bed.parcels, args.precision, device=dev)
     gas = mppic.gas_to_device(bed.U, None, args.precision, device=dev)
-    nsteps_all = args.warmup + args.steps
-    obj = torch.zeros((max(nsteps_all, args.sort1_steps, 2), 2), dtype=torch.float64, device=dev)
+    pre = settle_steps(args) + args.warmup
+    obj = torch.zeros((max(pre, args.steps, 2), 2), dtype=torch.float64, device=dev)
 
-    # warm-up steps, then exactly --steps timed steps in one call
-    if args.warmup:
-        b.step(parcels, gas, args.warmup, obj[: args.warmup])
+    # settling and warm-up steps, then exactly --steps timed steps in one call
+    if pre:
+        b.step(parcels, gas, pre, obj[:pre])
     b.check()
     barrier()
     clocks = Clocks(local)
@@ -221,7 +249,7 @@ def run_gpu(args):
     b.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    b.step(parcels, gas, args.steps, obj[args.warmup:])
+    b.step(parcels, gas, args.steps, obj[: args.steps])
     e1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -249,30 +277,35 @@ def run_gpu(args):
                 "bytes_per_launch": bpl, "ms_per_launch": round(step_ms, 5), "phase_ms": prof["ms"],
                 "phase_share": shares}
 
-    # the same bed sorted by cell every step (the other sort schedule of this workload)
-    sort1 = None
-    if args.sort1_steps > 0 and args.sort_every != 1:
-        b.tune(0, 1)
-        b.step(parcels, gas, 2, obj[:2])
+    # the same bed and window under the other sort schedule, on a fresh handle
+    alt = None
+    if args.alt_sort_every > 0 and args.alt_sort_every != args.sort_every:
+        b2 = mppic.Bed(bed.params, precision=args.precision, sort_every=args.alt_sort_every,
+                       stream=stream)
+        p2 = mppic.parcels_to_device(bed.parcels, args.precision, device=dev)
+        if pre:
+            b2.step(p2, gas, pre, obj[:pre])
+        b2.check()
         barrier()
-        b.profile(True)
+        b2.profile(True)
         h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0.record(stream)
-        b.step(parcels, gas, args.sort1_steps, obj[: args.sort1_steps])
+        b2.step(p2, gas, args.steps, obj[: args.steps])
         h1.record(stream)
         barrier()
-        pr1 = b.profile_read()
-        b.profile(False)
-        b.check()
-        sms = h0.elapsed_time(h1)
-        t1 = torch.tensor([sms], dtype=torch.float64, device=dev)
+        pr2 = b2.profile_read()
+        b2.profile(False)
+        b2.check()
+        t1 = torch.tensor([h0.elapsed_time(h1)], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(t1, op=dist.ReduceOp.MAX)
-        sort1 = {"value": world * bed.np * args.sort1_steps / (float(t1.item()) / 1e3), "unit": UNIT,
-                 "ms_per_step": float(t1.item()) / args.sort1_steps, "steps": args.sort1_steps,
-                 "sort_every": 1, "phase_ms_per_step": {k: round(v / args.sort1_steps, 4)
-                                                        for k, v in pr1["ms"].items()}}
-        b.tune(0, args.sort_every)
+        alt = {"sort_every": args.alt_sort_every,
+               "value": world * bed.np * args.steps / (float(t1.item()) / 1e3), "unit": UNIT,
+               "ms_per_step": float(t1.item()) / args.steps,
+               "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in pr2["ms"].items()}}
+        b2.close()
+        del p2
+        torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers: every step copies the parcel state in
     # from pinned host memory and the new state and objectives back out; the copies of the
@@ -385,7 +418,7 @@ def run_gpu(args):
                 "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
                 "config": workload_config(bed, args), "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": prof["total_launches"], "clocks": clk,
-                "fp64_form": fp64, "sort_every_step": sort1, "adjoint": adj,
+                "fp64_form": fp64, "alt_schedule": alt, "adjoint": adj,
                 "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(line))
     b.close()
@@ -408,7 +441,7 @@ def run_batched(args):
     batch = mppic.Batch([b.params for b in beds], [b.np for b in beds], precision=args.precision,
                         sort_every=args.sort_every, stream=stream)
     parcels, gas = mppic.concat_beds(beds, args.precision)
-    tuned = tune.autotune(batch, parcels, gas, steps=5, grids=(0, 1, 2), sorts=(5, 10, 20))
+    tuned = tune.autotune(batch, parcels, gas, steps=10, grids=(0, 1, 2), sorts=(1, 2, 5, 10))
     period = tuned["best"][1]
     rounds = max(1, args.steps // period)
     steps = rounds * period
@@ -525,7 +558,21 @@ def run_reference(args):
     import oracle
     oracle.build()
     bed = make_workload(args.workload, args.np, grid=args.grid)
-    sample, m = _sample(bed, max(1, args.cpu_sample // 4))
+    # the oracle's cost per step: a fixed part (the node fields of the whole grid) and a part
+    # per parcel; the sample per step is sized so that all warm-up and timed steps fit the
+    # budget
+    costs = []
+    for m0 in (2000, 20000):
+        smp, m0 = _sample(bed, m0)
+        t0 = time.perf_counter()
+        oracle.step(bed.params, smp, 1, U=bed.U, outputs=False)
+        costs.append((m0, time.perf_counter() - t0))
+    (ma, ta), (mb, tb) = costs
+    per = max((tb - ta) / max(mb - ma, 1), 1e-9)
+    fixed = max(ta - per * ma, 0.0)
+    budget = args.ref_seconds / max(args.steps + args.warmup, 1)
+    m_fit = int((budget - fixed) / per) if budget > fixed else 1000
+    sample, m = _sample(bed, min(max(1000, m_fit), max(1000, args.cpu_sample // 4)))
     state = sample
     for _ in range(args.warmup):
         state, _, _ = oracle.step(bed.params, state, 1, U=bed.U, outputs=False)
@@ -540,7 +587,8 @@ def run_reference(args):
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{m} of {bed.np} parcels per step, full grid"},
+                             "sample": f"{m} of {bed.np} parcels per step, full grid "
+                                       f"(sized for {args.ref_seconds:.0f} s of timed oracle steps)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
