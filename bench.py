@@ -71,7 +71,7 @@ def parse():
                     help="steps of the reverse-mode timing on the differentiation bed (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="parcels in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-seconds", type=float, default=150.0,
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="budget of the reference arm's timed oracle steps")
     args = ap.parse_args()
     if args.run_steps is None:
@@ -550,35 +550,60 @@ def cpu_baseline(bed, m, steps=2):
             "seconds": dt}
 
 
+def sub_column(bed, side):
+    """The bed's side x side x nz column of cells at the origin corner, with the parcels in it
+    (and the gas fields on its nodes): a bounded sample of the same workload."""
+    import numpy as np
+    from paper_2211_15605_gb300 import synth
+    p = bed.params
+    side = max(1, min(side, p["nx"], p["ny"]))
+    q = dict(p, nx=side, ny=min(side, p["ny"]))
+    keep = (bed.parcels["x"] < side * p["dx"]) & (bed.parcels["y"] < q["ny"] * p["dy"])
+    parcels = {k: np.ascontiguousarray(v[keep]) for k, v in bed.parcels.items()}
+    U = []
+    for u in bed.U:
+        if u is None:
+            U.append(None)
+            continue
+        g = np.asarray(u).reshape(p["nz"] + 1, p["ny"] + 1, p["nx"] + 1)
+        U.append(np.ascontiguousarray(g[:, : q["ny"] + 1, : side + 1]).ravel())
+    return synth.Bed(q, parcels, U=tuple(U), nsteps=bed.nsteps, meta=dict(bed.meta))
+
+
 def run_reference(args):
-    """Time the FP64 CPU oracle on a bounded sample per step (rank 0 only)."""
+    """Time the FP64 CPU oracle on a bounded sample per step (rank 0 only): a column of the
+    bed (full height) sized from a cost calibration so that the warm-up and timed steps fit
+    the budget."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
     bed = make_workload(args.workload, args.np, grid=args.grid)
-    # the oracle's cost per step: a fixed part (the node fields of the whole grid) and a part
-    # per parcel; the sample per step is sized so that all warm-up and timed steps fit the
-    # budget
+    p = bed.params
+    # the oracle's cost per step: a part per cell (the node fields) and a part per parcel
     costs = []
-    for m0 in (2000, 20000):
-        smp, m0 = _sample(bed, m0)
+    for side in (4, 8):
+        col = sub_column(bed, side)
         t0 = time.perf_counter()
-        oracle.step(bed.params, smp, 1, U=bed.U, outputs=False)
-        costs.append((m0, time.perf_counter() - t0))
-    (ma, ta), (mb, tb) = costs
-    per = max((tb - ta) / max(mb - ma, 1), 1e-9)
-    fixed = max(ta - per * ma, 0.0)
+        oracle.step(col.params, col.parcels, 1, U=col.U, outputs=False)
+        costs.append((col.params["nx"] * col.params["ny"] * p["nz"], col.np, time.perf_counter() - t0))
+    (ca, na, ta), (cb, nb, tb) = costs
+    dens = bed.np / (p["nx"] * p["ny"] * p["nz"])          # parcels per cell, whole bed
+    per_cell = max((tb - ta) / max(cb - ca, 1), 1e-12)      # cells and parcels grow together
     budget = args.ref_seconds / max(args.steps + args.warmup, 1)
-    m_fit = int((budget - fixed) / per) if budget > fixed else 1000
-    sample, m = _sample(bed, min(max(1000, m_fit), max(1000, args.cpu_sample // 4)))
-    state = sample
+    side = 4
+    for s_try in range(4, max(p["nx"], p["ny"]) + 1):
+        if per_cell * s_try * s_try * p["nz"] > budget:
+            break
+        side = s_try
+    col = sub_column(bed, side)
+    state, m = col.parcels, col.np
     for _ in range(args.warmup):
-        state, _, _ = oracle.step(bed.params, state, 1, U=bed.U, outputs=False)
+        state, _, _ = oracle.step(col.params, state, 1, U=col.U, outputs=False)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        state, _, _ = oracle.step(bed.params, state, 1, U=bed.U, outputs=False)
+        state, _, _ = oracle.step(col.params, state, 1, U=col.U, outputs=False)
     dt = time.perf_counter() - t0
     value = m * args.steps / dt
     cfg = workload_config(bed, args)
@@ -587,8 +612,10 @@ def run_reference(args):
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{m} of {bed.np} parcels per step, full grid "
-                                       f"(sized for {args.ref_seconds:.0f} s of timed oracle steps)"},
+                             "sample": f"the {col.params['nx']}x{col.params['ny']}x{p['nz']}-cell "
+                                       f"column at the origin corner with its {m} of {bed.np} "
+                                       f"parcels (bed mean {dens:.2f} per cell), sized for "
+                                       f"{args.ref_seconds:.0f} s of timed oracle steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

@@ -380,7 +380,7 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
     }
     if (local) {                // `cur` is laid out by the current cell starts
       const long long nb = h->nbricks;
-      const unsigned gb = (unsigned)(nb < 8LL * h->nsm ? nb : 8LL * h->nsm);
+      const unsigned gb = (unsigned)nb;            // one CTA per brick: empty ones exit at once
       CU(cudaMemsetAsync(h->rs_far, 0, sizeof(int) * nb, st));
       k_rs_hist<<<gb, RS_THREADS, 0, st>>>(h->keys[0], h->cstart, h->bgeo, nb, h->rs_cnt,
                                            h->rs_wcnt, h->rs_far);
