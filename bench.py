@@ -182,11 +182,11 @@ def measured_peak():
 # --------------------------------------------------------------- GPU arm --
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32 step kernel per
-# parcel, from one ncu capture on the 128x128x128 / 8M-parcel dense bed
-# (profiles/k_cells_float_dense_8M.md); the dense bed's traffic grows in proportion to its
-# parcels. Reported only while the kernel source is the one captured.
-STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 66.0,
-                "source_sha256": "7bc1e819831d1d4d5732ff946b6b55a375059756c5e394757149e5fd8b90bed0"}
+# parcel, from ncu captures on the 128x128x128 / 8M-parcel dense bed at step 5 (67.9 B) and
+# step 290 (68.9 B) of its run (profiles/k_cells_float_dense_8M.md): the mean over the run,
+# in proportion to the parcels. Reported only while the kernel source is the one captured.
+STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 68.4,
+                "source_sha256": "40658eb296caca515db37c98ae496733378254cb118c47f0b25ecf02c83f2504"}
 
 
 def step_traffic(args, np_):

@@ -11,7 +11,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmppic.so")
 SOURCES = [os.path.join(CSRC, "mppic.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "mppic_device.cuh"), os.path.join(CSRC, "mppic_adjoint.cuh"),
-               os.path.join(CSRC, "mppic_resort.cuh"), os.path.join(ROOT, "include", "mppic.h")]
+               os.path.join(CSRC, "mppic_sort.cuh"), os.path.join(CSRC, "mppic_resort.cuh"), os.path.join(ROOT, "include", "mppic.h")]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
               "-Xcompiler", "-fPIC", "-shared"]
 

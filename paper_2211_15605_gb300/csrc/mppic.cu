@@ -17,6 +17,7 @@
 #include "../../include/mppic.h"
 #include "mppic_adjoint.cuh"
 #include "mppic_device.cuh"
+#include "mppic_sort.cuh"
 #include "mppic_resort.cuh"
 
 using namespace mppic;
