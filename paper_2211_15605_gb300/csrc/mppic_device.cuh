@@ -467,36 +467,58 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Adds NV values at the 8 corners of cell (i,j,k) with in-cell coordinates x0..x2 in exact
-// fixed point, starting at quantity q0 (0 = Vs, 1 = A, then Bx, By, Bz): into the brick's
-// shared tile if the cell is in the brick (i0, j0, k0 = its first cell), else into the
-// global accumulators. Integer additions commute, so the order of these calls does not
-// change any sum. Used for parcels that are not in their sorted cell.
+// Adds NV values at the 8 corners of cell `cell` (cell_id) with in-cell coordinates x0..x2 in exact
+// fixed point, starting at quantity q0 (0 = Vs, 1 = A, then Bx, By, Bz), for every lane of
+// the warp in `pend` (a ballot, not 0; all 32 lanes call it): into the brick's shared tile
+// if the cell is in the brick (i0, j0, k0 = its first cell), else into the global
+// accumulators. Used for parcels that are not in their sorted cell. These are rare, so the
+// warp shares the work: in rounds of four such lanes, lanes 8g..8g+7 take the 8 corners of
+// the g-th, instead of each lane running its 8 corners while the rest of the warp idles.
+// Integer additions commute, so neither the order of these calls nor the rounds change any
+// sum.
 template <class T, int NV>
-__device__ __noinline__ void deposit_foreign(const KParams<T>& p, u64* fx, int* kr, int i0, int j0,
-                                             int k0, int i, int j, int k, T x0, T x1, T x2, int q0,
-                                             T v0, T v1, T v2, T v3) {
+__device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* fx, int* kr, int i0,
+                                                  int j0, int k0, unsigned pend, int cell, T x0, T x1,
+                                                  T x2, int q0, T v0, T v1, T v2, T v3) {
   constexpr int W = Words<T>::n;
-  const T vals[4] = {v0, v1, v2, v3};
-  const T w[3][2] = {{T(1) - x0, x0}, {T(1) - x1, x1}, {T(1) - x2, x2}};
-  const int ti = i - i0, tj = j - j0, tk = k - k0;
-  const bool in = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
-  atomicMin(kr, k);                              // node layers deposited into (shared)
-  atomicMax(kr + 1, k + 1);
-  for (int q = 0; q < 8; ++q) {
-    const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
-    const T Wq = (w[0][a] * w[1][b]) * w[2][c];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int qq = q0 + v;
-      u64 f[W];
-      to_fixed(vals[v] * Wq, qq == 0 ? p.mV : p.mA, f, p.errs);
-      if (in)
-        acc_add(fx + (qq * W) * TNODES + (ti + a) + TX * ((tj + b) + TY * (tk + c)), TNODES, f);
-      else
-        acc_add(p.acc + (long long)(qq * W) * p.nstride + p.nbase + node_id(p, i + a, j + b, k + c),
-                p.nstride, f);
+  const int lane = threadIdx.x & 31, g = lane >> 3, corner = lane & 7;
+  const int a = corner & 1, b = (corner >> 1) & 1, c = corner >> 2;
+  while (pend) {
+    unsigned m = pend;                           // the g-th lowest pending lane
+    for (int t = 0; t < g; ++t) m &= m - 1u;
+    const bool has = m != 0u;
+    const int s = has ? __ffs(m) - 1 : 0;
+    int si, sj, sk;
+    decode_cell(p, __shfl_sync(FULL, cell, s), si, sj, sk);
+    const T y0 = __shfl_sync(FULL, x0, s), y1 = __shfl_sync(FULL, x1, s), y2 = __shfl_sync(FULL, x2, s);
+    T vals[4];
+    vals[0] = __shfl_sync(FULL, v0, s);
+    if (NV > 1) {
+      vals[1] = __shfl_sync(FULL, v1, s);
+      vals[2] = __shfl_sync(FULL, v2, s);
+      vals[3] = __shfl_sync(FULL, v3, s);
     }
+    if (has) {
+      const T Wq = ((a ? y0 : T(1) - y0) * (b ? y1 : T(1) - y1)) * (c ? y2 : T(1) - y2);
+      const int ti = si - i0, tj = sj - j0, tk = sk - k0;
+      const bool in = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
+      if (corner == 0) {                         // node layers deposited into (shared)
+        atomicMin(kr, sk);
+        atomicMax(kr + 1, sk + 1);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int qq = q0 + v;
+        u64 f[W];
+        to_fixed(vals[v] * Wq, qq == 0 ? p.mV : p.mA, f, p.errs);
+        if (in)
+          acc_add(fx + (qq * W) * TNODES + (ti + a) + TX * ((tj + b) + TY * (tk + c)), TNODES, f);
+        else
+          acc_add(p.acc + (long long)(qq * W) * p.nstride + p.nbase + node_id(p, si + a, sj + b, sk + c),
+                  p.nstride, f);
+      }
+    }
+    for (int t = 0; t < 4; ++t) pend &= pend - 1u;
   }
 }
 
@@ -873,6 +895,11 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     cp_async_wait<PSTAGES - 1>();
     const bool act = n > r;
     const unsigned bal = __ballot_sync(FULL, act);
+    // parcels off their sorted cell: recorded here, deposited by the whole warp below
+    bool off_old = false, off_new = false;       // at the old position / the new one
+    int co = 0, cno = 0;                         // their cell ids
+    T xo[3] = {T(0), T(0), T(0)}, xno[3] = {T(0), T(0), T(0)};
+    T V = T(0), fd[4] = {T(0), T(0), T(0), T(0)};
     if (act) {
       const int q = off + __popc(bal & below);
       const T* slot = pre + (r % PSTAGES) * 8 * BCELLS + tid;
@@ -880,7 +907,11 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
       const T d = slot[6 * BCELLS], om = slot[7 * BCELLS];
       Cell3<T> c;
       const bool own = bin3_expect(p, x, y, z, ci, cj, ck, c);
-      const T V = om * (d * d * d) * p.vcoef;
+      V = om * (d * d * d) * p.vcoef;
+      if (!own) {
+        co = cell_id(p, c.i, c.j, c.k);
+        xo[0] = c.xi[0]; xo[1] = c.xi[1]; xo[2] = c.xi[2];
+      }
       if (MODE == 0) {
         if (own) {
           W8<T> Wq;
@@ -888,8 +919,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
           corner_weights(c.xi, Wq, yz);
           sums.add_vol(V, Wq);
         } else {
-          deposit_foreign<T, 1>(p, fx, s_kr, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 0,
-                                V, T(0), T(0), T(0));
+          off_old = true;
         }
       } else {
         const T u = slot[3 * BCELLS], v = slot[4 * BCELLS], w = slot[5 * BCELLS];
@@ -918,8 +948,8 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         if (own) {
           sums.add_drag(f, f * u, f * v, f * w, wt.W);
         } else {
-          deposit_foreign<T, 4>(p, fx, s_kr, bi0, bj0, bk0, c.i, c.j, c.k, c.xi[0], c.xi[1], c.xi[2], 1,
-                                f, f * u, f * v, f * w);
+          off_old = true;
+          fd[0] = f; fd[1] = f * u; fd[2] = f * v; fd[3] = f * w;
         }
         // semi-implicit push (Eq. 4 / (eps_P rho_P), drag implicit), Eq. 3, specular walls
         T pos[3] = {x, y, z};
@@ -938,16 +968,17 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
           up[a] = un;
         }
         if (bad) atomicOr(p.errs, ERR_DOMAIN);
-        Cell3<T> cn;
         // solids volume of the new position, for the next step
+        Cell3<T> cn;
         if (bin3_expect(p, pos[0], pos[1], pos[2], ci, cj, ck, cn)) {
           W8<T> Wq;
           T yz[4];
           corner_weights(cn.xi, Wq, yz);
           sums.add_vol(V, Wq);
         } else {
-          deposit_foreign<T, 1>(p, fx, s_kr, bi0, bj0, bk0, cn.i, cn.j, cn.k, cn.xi[0], cn.xi[1],
-                                cn.xi[2], 0, V, T(0), T(0), T(0));
+          off_new = true;
+          cno = cell_id(p, cn.i, cn.j, cn.k);
+          xno[0] = cn.xi[0]; xno[1] = cn.xi[1]; xno[2] = cn.xi[2];
         }
         dst.a[0][q] = pos[0]; dst.a[1][q] = pos[1]; dst.a[2][q] = pos[2];
         dst.a[3][q] = up[0]; dst.a[4][q] = up[1]; dst.a[5][q] = up[2];
@@ -959,6 +990,21 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         if (cell_out) cell_out[q] = cell_id(p, cn.i, cn.j, cn.k);
         if (key_out) key_out[q] = (uint32_t)(p.bbase * BCELLS) + brick_key(p, cn.i, cn.j, cn.k);
       }
+    }
+    {
+      const unsigned po = __ballot_sync(FULL, off_old);
+      if (po) {
+        if (MODE == 0)
+          deposit_foreign_warp<T, 1>(p, fx, s_kr, bi0, bj0, bk0, po, co, xo[0], xo[1], xo[2], 0, V,
+                                     T(0), T(0), T(0));
+        else
+          deposit_foreign_warp<T, 4>(p, fx, s_kr, bi0, bj0, bk0, po, co, xo[0], xo[1], xo[2], 1, fd[0],
+                                     fd[1], fd[2], fd[3]);
+      }
+      const unsigned pn = MODE == 1 ? __ballot_sync(FULL, off_new) : 0u;
+      if (pn)
+        deposit_foreign_warp<T, 1>(p, fx, s_kr, bi0, bj0, bk0, pn, cno, xno[0], xno[1], xno[2], 0, V,
+                                   T(0), T(0), T(0));
     }
     off += __popc(bal);
   }
