@@ -183,11 +183,12 @@ def measured_peak():
 # --------------------------------------------------------------- GPU arm --
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32 step kernel per
-# parcel, from ncu captures on the 128x128x128 / 8M-parcel dense bed at step 5 (67.9 B) and
-# step 290 (68.9 B) of its run (profiles/k_cells_float_dense_8M.md): the mean over the run,
-# in proportion to the parcels. Reported only while the kernel source is the one captured.
-STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 68.4,
-                "source_sha256": "40658eb296caca515db37c98ae496733378254cb118c47f0b25ecf02c83f2504"}
+# parcel, from ncu captures on the 128x128x128 / 8M-parcel dense bed sorted every 2 steps:
+# step 5 (59.0 B), step 290 (after a sort, 65.2 B) and step 291 (drifted, 62.0 B)
+# (profiles/k_cells_float_dense_8M.md); their mean, in proportion to the parcels. Reported
+# only while the kernel source is the one captured.
+STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 62.1,
+                "source_sha256": "2056b2b462a0c175c3e5fb32d14f29548a4bff113e1cba77f7c3cdd32f6d1854"}
 
 
 def step_traffic(args, np_):
