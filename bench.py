@@ -15,8 +15,9 @@ states the window.
 
 Prints one JSON line. `value` is whole-job parcel-updates/s with inputs resident in HBM
 (CUDA events on the library's stream around exactly --steps steps). `e2e` is the same
-metric through the C ABI with the parcel state copied from pinned host memory before and
-back after every step. `roofline` is the fused step kernel's algorithmic bytes per launch
+metric through the C ABI with a parcel state copied in from pinned host memory and the new
+state copied back out every step (pipelined: one step's kernels overlap the next upload
+and the previous download). `roofline` is the fused step kernel's algorithmic bytes per launch
 over its event-timed duration against the measured HBM copy bandwidth. `cpu_baseline` is
 the FP64 CPU oracle on a bounded sample of the same bed. `alt_schedule` times the same bed
 over the same window sorted every 1 and every 10 steps (the schedules this workload
@@ -67,7 +68,7 @@ def parse():
                          "handle (comma list; 0 = none)")
     ap.add_argument("--precision", type=int, choices=(32, 64), default=32)
     ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64-form comparison (0 = skip)")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--adjoint-steps", type=int, default=200,
                     help="steps of the reverse-mode timing on the differentiation bed (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="parcels in the CPU-oracle sample")
@@ -310,36 +311,47 @@ def run_gpu(args):
         del p2
         torch.cuda.empty_cache()
 
-    # end to end through the C ABI with host buffers: every step copies the parcel state in
-    # from pinned host memory and the new state and objectives back out; the copies of the
-    # arrays are spread over two copy streams (both directions), ordered around the step
+    # end to end through the C ABI with host buffers: every step copies a parcel state in from
+    # pinned host memory (all 8 arrays) and its new state and objectives back out (6 arrays +
+    # 2 doubles). Steps are pipelined over two device buffer sets: the upload of step k+1 and
+    # the download of step k-1 run on the copy engines while step k's kernels run.
     e2e = None
     if args.e2e_steps > 0:
         fields = mppic.PARCEL_FIELDS
+        outs = ("x", "y", "z", "u", "v", "w")
         host = {k: parcels[k].cpu().pin_memory() for k in fields}
-        out_host = {k: torch.empty_like(host[k]).pin_memory() for k in ("x", "y", "z", "u", "v", "w")}
-        obj_host = torch.empty((1, 2), dtype=torch.float64).pin_memory()
-        copy_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+        bufs = [parcels, {k: torch.empty_like(v) for k, v in parcels.items()}]
+        out_host = [{k: torch.empty_like(host[k]).pin_memory() for k in outs} for _ in range(2)]
+        obj_host = [torch.empty((1, 2), dtype=torch.float64).pin_memory() for _ in range(2)]
+        obj2 = [torch.zeros((1, 2), dtype=torch.float64, device=dev) for _ in range(2)]
+        up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        ev = lambda: torch.cuda.Event()
+        up_done, step_done, down_done = [ev(), ev()], [ev(), ev()], [ev(), ev()]
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(args.e2e_steps):
-            for cs in copy_streams:
-                cs.wait_stream(stream)
-            for i, k in enumerate(fields):
-                with torch.cuda.stream(copy_streams[i % 2]):
-                    parcels[k].copy_(host[k], non_blocking=True)
-            for cs in copy_streams:
-                stream.wait_stream(cs)
-            o = b.step(parcels, gas, 1, obj[:1])
-            for cs in copy_streams:
-                cs.wait_stream(stream)
-            for i, k in enumerate(out_host):
-                with torch.cuda.stream(copy_streams[i % 2]):
-                    out_host[k].copy_(parcels[k], non_blocking=True)
-            obj_host.copy_(o, non_blocking=True)
-            for cs in copy_streams:
-                stream.wait_stream(cs)
+        up.wait_stream(stream)
+        down.wait_stream(stream)
+        for k in range(args.e2e_steps):
+            s = k % 2
+            X = bufs[s]
+            if k >= 2:
+                up.wait_event(down_done[s])          # the buffer's previous state is out
+            with torch.cuda.stream(up):
+                for f in fields:
+                    X[f].copy_(host[f], non_blocking=True)
+                up_done[s].record(up)
+            stream.wait_event(up_done[s])
+            b.step(X, gas, 1, obj2[s])
+            step_done[s].record(stream)
+            down.wait_event(step_done[s])
+            with torch.cuda.stream(down):
+                for f in outs:
+                    out_host[s][f].copy_(X[f], non_blocking=True)
+                obj_host[s].copy_(obj2[s], non_blocking=True)
+                down_done[s].record(down)
+        stream.wait_stream(up)
+        stream.wait_stream(down)
         f1.record(stream)
         barrier()
         ems = f0.elapsed_time(f1)
@@ -349,8 +361,9 @@ def run_gpu(args):
         tsz = 4 if args.precision == 32 else 8
         e2e = {"value": world * bed.np * args.e2e_steps / (float(t2.item()) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": bed.np * 8 * tsz, "d2h_bytes_per_step": bed.np * 6 * tsz + 16,
-               "steps": args.e2e_steps, "copy_streams": len(copy_streams)}
+               "steps": args.e2e_steps, "pipelined": "2 device buffer sets; uploads, kernels and downloads overlap"}
         b.check()
+        del bufs
 
     # FP64 form on the same bed, for the FP32-vs-FP64 comparison
     fp64 = None
