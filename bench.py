@@ -16,8 +16,8 @@ states the window.
 Prints one JSON line. `value` is whole-job parcel-updates/s with inputs resident in HBM
 (CUDA events on the library's stream around exactly --steps steps). `e2e` is the same
 metric through the C ABI with a parcel state copied in from pinned host memory and the new
-state copied back out every step (pipelined: one step's kernels overlap the next upload
-and the previous download). `roofline` is the fused step kernel's algorithmic bytes per launch
+state copied back out every step (pipelined over three device buffer sets: one step's
+kernels overlap the next uploads and the previous downloads). `roofline` is the fused step kernel's algorithmic bytes per launch
 over its event-timed duration against the measured HBM copy bandwidth. `cpu_baseline` is
 the FP64 CPU oracle on a bounded sample of the same bed. `alt_schedule` times the same bed
 over the same window sorted every 1 and every 10 steps (the schedules this workload
@@ -235,7 +235,10 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     bed = make_workload(args.workload, args.np, seed_offset=rank, grid=args.grid)
-    stream = torch.cuda.current_stream()
+    # a stream of its own: the legacy default stream would order the end-to-end leg's copies
+    # behind the library's kernels
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     b = mppic.Bed(bed.params, precision=args.precision, sort_every=args.sort_every, stream=stream)
     parcels = mppic.parcels_to_device(bed.parcels, args.precision, device=dev)
     gas = mppic.gas_to_device(bed.U, None, args.precision, device=dev)
@@ -313,29 +316,31 @@ def run_gpu(args):
 
     # end to end through the C ABI with host buffers: every step copies a parcel state in from
     # pinned host memory (all 8 arrays) and its new state and objectives back out (6 arrays +
-    # 2 doubles). Steps are pipelined over two device buffer sets: the upload of step k+1 and
-    # the download of step k-1 run on the copy engines while step k's kernels run.
+    # 2 doubles). Steps are pipelined over three device buffer sets: the uploads of the next
+    # steps and the downloads of the previous ones run on the copy engines (both directions at
+    # once) while step k's kernels run; with two sets the upload of step k+2 would wait for
+    # the download of step k, which waits for step k's kernels.
     e2e = None
     if args.e2e_steps > 0:
         fields = mppic.PARCEL_FIELDS
         outs = ("x", "y", "z", "u", "v", "w")
         host = {k: parcels[k].cpu().pin_memory() for k in fields}
-        bufs = [parcels, {k: torch.empty_like(v) for k, v in parcels.items()}]
-        out_host = [{k: torch.empty_like(host[k]).pin_memory() for k in outs} for _ in range(2)]
-        obj_host = [torch.empty((1, 2), dtype=torch.float64).pin_memory() for _ in range(2)]
-        obj2 = [torch.zeros((1, 2), dtype=torch.float64, device=dev) for _ in range(2)]
+        NB = 3
+        bufs = [parcels] + [{k: torch.empty_like(v) for k, v in parcels.items()} for _ in range(NB - 1)]
+        out_host = [{k: torch.empty_like(host[k]).pin_memory() for k in outs} for _ in range(NB)]
+        obj_host = [torch.empty((1, 2), dtype=torch.float64).pin_memory() for _ in range(NB)]
+        obj2 = [torch.zeros((1, 2), dtype=torch.float64, device=dev) for _ in range(NB)]
         up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-        ev = lambda: torch.cuda.Event()
-        up_done, step_done, down_done = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+        up_done, step_done, down_done = ([torch.cuda.Event() for _ in range(NB)] for _ in range(3))
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         up.wait_stream(stream)
         down.wait_stream(stream)
         for k in range(args.e2e_steps):
-            s = k % 2
+            s = k % NB
             X = bufs[s]
-            if k >= 2:
+            if k >= NB:
                 up.wait_event(down_done[s])          # the buffer's previous state is out
             with torch.cuda.stream(up):
                 for f in fields:
@@ -361,7 +366,7 @@ def run_gpu(args):
         tsz = 4 if args.precision == 32 else 8
         e2e = {"value": world * bed.np * args.e2e_steps / (float(t2.item()) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": bed.np * 8 * tsz, "d2h_bytes_per_step": bed.np * 6 * tsz + 16,
-               "steps": args.e2e_steps, "pipelined": "2 device buffer sets; uploads, kernels and downloads overlap"}
+               "steps": args.e2e_steps, "pipelined": "3 device buffer sets; uploads, kernels and downloads overlap"}
         b.check()
         del bufs
 
