@@ -182,6 +182,34 @@ __device__ __forceinline__ void decode_cell(const KParams<T>& p, int c, int& i, 
   k = r / p.ny;
 }
 
+// Cell (i,j,k) as bit fields of cb[0] and cb[1] bits for i and j (cb[0] < 0: the cell id,
+// for a grid whose fields would not fit 31 bits). Unpacking is shifts, not divisions.
+struct CellBits {
+  int b0, b1;
+};
+template <class T>
+__device__ __forceinline__ CellBits cell_bits(const KParams<T>& p) {
+  auto bits = [](int n) { return n > 1 ? 32 - __clz(n - 1) : 0; };
+  CellBits cb{bits(p.nx), bits(p.ny)};
+  if (cb.b0 + cb.b1 + bits(p.nz) > 31) cb.b0 = -1;
+  return cb;
+}
+template <class T>
+__device__ __forceinline__ int pack_cell(const KParams<T>& p, CellBits cb, int i, int j, int k) {
+  return cb.b0 >= 0 ? (i | (j << cb.b0) | (k << (cb.b0 + cb.b1))) : cell_id(p, i, j, k);
+}
+template <class T>
+__device__ __forceinline__ void unpack_cell(const KParams<T>& p, CellBits cb, int c, int& i, int& j,
+                                            int& k) {
+  if (cb.b0 >= 0) {
+    i = c & ((1 << cb.b0) - 1);
+    j = (c >> cb.b0) & ((1 << cb.b1) - 1);
+    k = c >> (cb.b0 + cb.b1);
+  } else {
+    decode_cell(p, c, i, j, k);
+  }
+}
+
 // Brick-major sort key of cell (i,j,k).
 template <class T>
 __device__ __forceinline__ uint32_t brick_key(const KParams<T>& p, int i, int j, int k) {
@@ -467,7 +495,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Adds NV values at the 8 corners of cell `cell` (cell_id) with in-cell coordinates x0..x2 in exact
+// Adds NV values at the 8 corners of cell `cell` (pack_cell) with in-cell coordinates x0..x2 in exact
 // fixed point, starting at quantity q0 (0 = Vs, 1 = A, then Bx, By, Bz), for every lane of
 // the warp in `pend` (a ballot, not 0; all 32 lanes call it): into the brick's shared tile
 // if the cell is in the brick (i0, j0, k0 = its first cell), else into the global
@@ -478,7 +506,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // sum.
 template <class T, int NV>
 __device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* fx, int* kr, int i0,
-                                                  int j0, int k0, unsigned pend, int cell, T x0, T x1,
+                                                  int j0, int k0, unsigned pend, CellBits cb, int cell, T x0, T x1,
                                                   T x2, int q0, T v0, T v1, T v2, T v3) {
   constexpr int W = Words<T>::n;
   const int lane = threadIdx.x & 31, g = lane >> 3, corner = lane & 7;
@@ -489,7 +517,7 @@ __device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* f
     const bool has = m != 0u;
     const int s = has ? __ffs(m) - 1 : 0;
     int si, sj, sk;
-    decode_cell(p, __shfl_sync(FULL, cell, s), si, sj, sk);
+    unpack_cell(p, cb, __shfl_sync(FULL, cell, s), si, sj, sk);
     const T y0 = __shfl_sync(FULL, x0, s), y1 = __shfl_sync(FULL, x1, s), y2 = __shfl_sync(FULL, x2, s);
     T vals[4];
     vals[0] = __shfl_sync(FULL, v0, s);
@@ -821,6 +849,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   const int bi0 = (int)(bu % (unsigned)p.nbx) * BX;
   const int bj0 = (int)((bu / (unsigned)p.nbx) % (unsigned)p.nby) * BY;
   const int bk0 = (int)(bu / ((unsigned)p.nbx * (unsigned)p.nby)) * BZ;
+  const CellBits cb = cell_bits(p);
   const long long kbase = b * BCELLS;
   if (p.cstart[kbase] == p.cstart[kbase + BCELLS]) {
     if (MODE == 1 && tid == 0) { obj_part[3 * b] = 0; obj_part[3 * b + 1] = 0; obj_part[3 * b + 2] = 0; }
@@ -909,7 +938,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
       const bool own = bin3_expect(p, x, y, z, ci, cj, ck, c);
       V = om * (d * d * d) * p.vcoef;
       if (!own) {
-        co = cell_id(p, c.i, c.j, c.k);
+        co = pack_cell(p, cb, c.i, c.j, c.k);
         xo[0] = c.xi[0]; xo[1] = c.xi[1]; xo[2] = c.xi[2];
       }
       if (MODE == 0) {
@@ -977,7 +1006,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
           sums.add_vol(V, Wq);
         } else {
           off_new = true;
-          cno = cell_id(p, cn.i, cn.j, cn.k);
+          cno = pack_cell(p, cb, cn.i, cn.j, cn.k);
           xno[0] = cn.xi[0]; xno[1] = cn.xi[1]; xno[2] = cn.xi[2];
         }
         dst.a[0][q] = pos[0]; dst.a[1][q] = pos[1]; dst.a[2][q] = pos[2];
@@ -995,15 +1024,15 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
       const unsigned po = __ballot_sync(FULL, off_old);
       if (po) {
         if (MODE == 0)
-          deposit_foreign_warp<T, 1>(p, fx, s_kr, bi0, bj0, bk0, po, co, xo[0], xo[1], xo[2], 0, V,
+          deposit_foreign_warp<T, 1>(p, fx, s_kr, bi0, bj0, bk0, po, cb, co, xo[0], xo[1], xo[2], 0, V,
                                      T(0), T(0), T(0));
         else
-          deposit_foreign_warp<T, 4>(p, fx, s_kr, bi0, bj0, bk0, po, co, xo[0], xo[1], xo[2], 1, fd[0],
+          deposit_foreign_warp<T, 4>(p, fx, s_kr, bi0, bj0, bk0, po, cb, co, xo[0], xo[1], xo[2], 1, fd[0],
                                      fd[1], fd[2], fd[3]);
       }
       const unsigned pn = MODE == 1 ? __ballot_sync(FULL, off_new) : 0u;
       if (pn)
-        deposit_foreign_warp<T, 1>(p, fx, s_kr, bi0, bj0, bk0, pn, cno, xno[0], xno[1], xno[2], 0, V,
+        deposit_foreign_warp<T, 1>(p, fx, s_kr, bi0, bj0, bk0, pn, cb, cno, xno[0], xno[1], xno[2], 0, V,
                                    T(0), T(0), T(0));
     }
     off += __popc(bal);
