@@ -185,11 +185,11 @@ def measured_peak():
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32 step kernel per
 # parcel, from ncu captures on the 128x128x128 / 8M-parcel dense bed sorted every 2 steps:
-# step 5 (59.0 B), step 290 (after a sort, 65.2 B) and step 291 (drifted, 62.0 B)
+# step 5 (58.9 B), step 290 (after a sort, 65.2 B) and step 291 (drifted, 61.9 B)
 # (profiles/k_cells_float_dense_8M.md); their mean, in proportion to the parcels. Reported
 # only while the kernel source is the one captured.
-STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 62.1,
-                "source_sha256": "2056b2b462a0c175c3e5fb32d14f29548a4bff113e1cba77f7c3cdd32f6d1854"}
+STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 62.0,
+                "source_sha256": "1b92b484cebdf160905e586ce70a27b5f84843ff04213d8bb6ed9169f1736def"}
 
 
 def step_traffic(args, np_):
@@ -332,6 +332,9 @@ def run_gpu(args):
         obj2 = [torch.zeros((1, 2), dtype=torch.float64, device=dev) for _ in range(NB)]
         up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
         up_done, step_done, down_done = ([torch.cuda.Event() for _ in range(NB)] for _ in range(3))
+        # a state that arrives from the host each step is sorted at the start of its step: its
+        # order is the sender's, not the layout of the handle's last sort
+        b.tune(0, 1)
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -359,6 +362,7 @@ def run_gpu(args):
         stream.wait_stream(down)
         f1.record(stream)
         barrier()
+        b.tune(0, args.sort_every)
         ems = f0.elapsed_time(f1)
         t2 = torch.tensor([ems], dtype=torch.float64, device=dev)
         if world > 1:
@@ -366,7 +370,8 @@ def run_gpu(args):
         tsz = 4 if args.precision == 32 else 8
         e2e = {"value": world * bed.np * args.e2e_steps / (float(t2.item()) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": bed.np * 8 * tsz, "d2h_bytes_per_step": bed.np * 6 * tsz + 16,
-               "steps": args.e2e_steps, "pipelined": "3 device buffer sets; uploads, kernels and downloads overlap"}
+               "steps": args.e2e_steps, "sort_every": 1,
+               "pipelined": "3 device buffer sets; uploads, kernels and downloads overlap"}
         b.check()
         del bufs
 

@@ -116,11 +116,17 @@ mppic_status mppic_create(const mppic_config *cfg, int nbeds, const long long *b
 /* Step a1-a3 (binning; optional sort by cell). Writes parcels->cell from the positions
  * with the exact FP64 formula i = clamp(floor(fl64(x * fl64(1/dx))), 0, nx-1).
  * If do_sort != 0, sorts all parcel arrays by cell and records the cell ranges in the
- * handle. The order: cells are grouped in bricks of 8x8x4 (brick-major), each brick in four
- * groups of 32 cells (local cell index i + 8 (j + 8 k), 32 per group); within a group the
- * parcels are stored by level: the r-th parcel of every cell of the group that has more
- * than r parcels, in cell order, then level r + 1. Within a cell parcels keep their
- * previous relative order (stable). parcels->cell is in the new order. */
+ * handle. The order: cells are grouped in bricks of 8x8x4 (brick-major), each brick in eight
+ * groups of 32 cells, taken in local cell order i + 8 (j + 8 k), or, where that saves more
+ * than a quarter of the warp iterations (the sum over groups of the group's largest count),
+ * ranked by parcel count (descending, ties by local cell index); within a group the parcels
+ * are stored by level: the r-th parcel of every cell of the group that has more than r
+ * parcels, in group order, then level r + 1. Within a cell parcels keep their previous
+ * relative order (stable). parcels->cell is in the new order.
+ * When the arrays hold the layout of the handle's last sort (as the last mppic_step or
+ * mppic_bin left them), the sort starts from it and is local (each brick from its own range
+ * and its 26 neighbours'); the result is the same stable order for any input order, only
+ * the cost depends on it. */
 mppic_status mppic_bin(mppic_handle *h, mppic_parcels *parcels, int do_sort);
 
 /* Steps a4-a5: deposit the solids volume of every parcel (V = w pi (s_d d)^3 / 6, trilinear

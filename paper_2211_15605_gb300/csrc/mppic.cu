@@ -360,13 +360,16 @@ mppic_status ensure_capacity(mppic_handle* h, long long np, bool want_pid) {
 // copy, and rebuild the cell ranges. Leaves the sorted copy as the parcel source.
 template <class T>
 mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays<T> cur,
-                               bool keys_ready = false, bool local = false) {
+                               bool keys_ready = false, bool local = false,
+                               const mppic_gas* gas = nullptr) {
   const long long np = pc->np;
   mppic_status s = ensure_capacity(h, np, pc->pid != nullptr);
   if (s) return s;
   KParams<T> p = make_params<T>(h, nullptr);
   const KParams<T>* beds = nullptr;
-  s = upload_beds<T>(h, nullptr, &beds);
+  // the sort reads no gas field; a step passes its own, so the per-bed parameters it uploads
+  // are the ones the step uses next (an upload waits for the stream)
+  s = upload_beds<T>(h, gas, &beds);
   if (s) return s;
   cudaStream_t st = h->stream;
   Phase ph(h, PH_SORT);
@@ -608,7 +611,7 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   if (!h->order_on_caller || h->order_np != np || sort_due(h->step_counter)) {
     // the caller's arrays still hold the last step's layout: re-sort locally
     const bool local = h->order_on_caller && h->order_np == np;
-    mppic_status s = sort_into_scratch<T>(h, pc, dst, false, local);
+    mppic_status s = sort_into_scratch<T>(h, pc, dst, false, local, gas);
     if (s) return s;
     src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
   }
@@ -623,7 +626,7 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   for (int it = 0; it < nsteps; ++it) {
     if (it > 0 && sort_due(h->step_counter + it)) {
-      s = sort_into_scratch<T>(h, pc, dst, true, true);   // keys from the previous step
+      s = sort_into_scratch<T>(h, pc, dst, true, true, gas);   // keys from the previous step
       if (s) return s;
       src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
     }

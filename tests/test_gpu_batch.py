@@ -89,3 +89,24 @@ def test_graph_replay_equals_eager_and_tuning_keeps_results():
     assert torch.allclose(o1, o_ref, rtol=1e-12, atol=0) and torch.allclose(obj, o_ref2, rtol=1e-12, atol=0)
     res = tune.autotune(g, d_g, gas_g, steps=3, grids=(0, 1), sorts=(3, 6))
     assert res["best"] in res["ms_per_step"]
+
+
+def test_graph_replay_with_gas_fields_equals_eager():
+    """A batch with prescribed gas velocity fields: the sort and the step upload the same
+    per-bed parameters, so a captured multi-step call (sorts included) replays as eager."""
+    beds = [synth.fourier_bed(n=n, nx=g[0], ny=g[1], nz=g[2], nsteps=1, seed=300 + k)
+            for k, (g, n) in enumerate((((16, 16, 24), 20000), ((9, 13, 20), 7000), ((24, 8, 16), 12000)))]
+    steps = 6
+    ref = mppic.Batch([b.params for b in beds], [b.np for b in beds], precision=32, sort_every=2)
+    d_ref, gas = mppic.concat_beds(beds, 32)
+    assert gas is not None
+    o_ref = ref.step(d_ref, gas, steps).clone()
+    ref.check()
+    g = mppic.Batch([b.params for b in beds], [b.np for b in beds], precision=32, sort_every=2)
+    d_g, gas_g = mppic.concat_beds(beds, 32)
+    obj = torch.empty((steps, len(beds), 2), dtype=torch.float64, device="cuda")
+    g.step_graph(d_g, gas_g, steps, obj)
+    g.check()
+    for f in ("x", "y", "z", "u", "v", "w"):
+        assert torch.equal(d_g[f], d_ref[f]), f
+    assert torch.allclose(obj, o_ref, rtol=1e-12, atol=0)
