@@ -189,7 +189,7 @@ def measured_peak():
 # (profiles/k_cells_float_dense_8M.md); their mean, in proportion to the parcels. Reported
 # only while the kernel source is the one captured.
 STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 62.0,
-                "source_sha256": "1b92b484cebdf160905e586ce70a27b5f84843ff04213d8bb6ed9169f1736def"}
+                "source_sha256": "353303b3bc7bc54dd41ca9a45a6c319b4679643c255a57d9e9a46820e1d59b4e"}
 
 
 def step_traffic(args, np_):

@@ -785,7 +785,7 @@ __device__ void cta_sum3(T a, T b, T c, T* sm, double* out) {
 // The cell kernel. One CTA owns one brick (taken from a work counter: persistent grid);
 // thread t owns the cell cellmap gives it (its own cell, or the cell of count rank t),
 // warp w the group of threads 32w..32w+31, whose parcels are stored by level
-// (k_level_gather). The warp's r-th iteration processes the r-th parcel of
+// (level_layout, at each sort). The warp's r-th iteration processes the r-th parcel of
 // each of its cells that has one, one per thread, with coalesced loads and stores.
 // MODE 0: deposit the solids volume of the current positions.
 // MODE 1: one full step (interp from a shared node-field tile, drag, drag sums,
