@@ -582,9 +582,9 @@ def sub_column(bed, side):
     import numpy as np
     from paper_2211_15605_gb300 import synth
     p = bed.params
-    side = max(1, min(side, p["nx"], p["ny"]))
-    q = dict(p, nx=side, ny=min(side, p["ny"]))
-    keep = (bed.parcels["x"] < side * p["dx"]) & (bed.parcels["y"] < q["ny"] * p["dy"])
+    side = max(1, side)
+    q = dict(p, nx=min(side, p["nx"]), ny=min(side, p["ny"]))
+    keep = (bed.parcels["x"] < q["nx"] * p["dx"]) & (bed.parcels["y"] < q["ny"] * p["dy"])
     parcels = {k: np.ascontiguousarray(v[keep]) for k, v in bed.parcels.items()}
     U = []
     for u in bed.U:
@@ -592,7 +592,7 @@ def sub_column(bed, side):
             U.append(None)
             continue
         g = np.asarray(u).reshape(p["nz"] + 1, p["ny"] + 1, p["nx"] + 1)
-        U.append(np.ascontiguousarray(g[:, : q["ny"] + 1, : side + 1]).ravel())
+        U.append(np.ascontiguousarray(g[:, : q["ny"] + 1, : q["nx"] + 1]).ravel())
     return synth.Bed(q, parcels, U=tuple(U), nsteps=bed.nsteps, meta=dict(bed.meta))
 
 
