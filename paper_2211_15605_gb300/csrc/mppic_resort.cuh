@@ -1,5 +1,5 @@
-// Local re-sort: the stable sort of the parcels by brick-major cell key (the binning and
-// sorting step that precedes the deposit, Sec. 2.2) when the parcels are already laid out
+// Local re-sort: the stable sort of the parcels by brick-major cell key (the sort by cell
+// that precedes the deposit, this library's own step) when the parcels are already laid out
 // by the previous sort, so that each brick's parcels occupy the range of sorted positions
 // the cell starts give it. Between two sorts a parcel moves a fraction of a cell per step,
 // so almost every parcel's new brick is its range's brick or one of that brick's 26

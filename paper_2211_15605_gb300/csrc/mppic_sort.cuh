@@ -1,5 +1,6 @@
-// Sorting the parcels by brick-major cell key from an arbitrary order (the binning and
-// sorting step that precedes the deposit, Sec. 2.2): a stable LSD radix sort of the keys
+// Sorting the parcels by brick-major cell key from an arbitrary order, before the deposit
+// (the paper locates each parcel's cell with index arithmetic, Sec. 2.2.3; ordering the
+// parcels by cell is this library's own step): a stable LSD radix sort of the keys
 // with the parcel index as value, the first sorted position of each key, and the level
 // layout of each brick's parcels that the cell kernel reads (level_layout, shared with the
 // local re-sort in mppic_resort.cuh).
