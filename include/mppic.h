@@ -95,7 +95,11 @@ typedef struct {
 } mppic_gas;
 
 /* Create a handle for one bed (nbeds = 1; bed_parcel_offsets and per_bed may be NULL) or
- * for a batch of nbeds independent beds advanced together. For a batch:
+ * for a batch of nbeds independent beds advanced together. Sec. 2.2.1: the paper passes the
+ * model parameters to the solver once at initialisation and afterwards only the time step
+ * crosses the boundary; here the parameters are fixed at creation (mppic_set_params and
+ * mppic_tune change the few that a caller varies) and the step calls carry only device
+ * pointers and a step count. For a batch:
  *   - per_bed (host, nbeds configs) gives each bed's grid and physics; precision and
  *     sort_every come from cfg;
  *   - bed_parcel_offsets (host, nbeds+1, starting at 0) gives each bed's parcel range in
@@ -113,8 +117,11 @@ typedef struct {
 mppic_status mppic_create(const mppic_config *cfg, int nbeds, const long long *bed_parcel_offsets,
                           const mppic_config *per_bed, void *stream, mppic_handle **out);
 
-/* Step a1-a3 (binning; optional sort by cell). Writes parcels->cell from the positions
- * with the exact FP64 formula i = clamp(floor(fl64(x * fl64(1/dx))), 0, nx-1).
+/* Step a1-a3 (binning; optional sort by cell). Sec. 2.2.3: the paper locates each parcel's
+ * computation cell through rank-1 index tensors; Sec. 3.1: the hard conditionals near cell
+ * faces and walls decide results bit by bit, so binning here is one exact formula that every
+ * form shares. Writes parcels->cell from the positions with the exact FP64 formula
+ * i = clamp(floor(fl64(x * fl64(1/dx))), 0, nx-1).
  * If do_sort != 0, sorts all parcel arrays by cell and records the cell ranges in the
  * handle. The order: cells are grouped in bricks of 8x8x4 (brick-major), each brick in eight
  * groups of 32 cells, taken in local cell order i + 8 (j + 8 k), or, where that saves more
@@ -137,7 +144,9 @@ mppic_status mppic_bin(mppic_handle *h, mppic_parcels *parcels, int do_sort);
 mppic_status mppic_deposit(mppic_handle *h, const mppic_parcels *parcels, const mppic_gas *gas,
                            double *Vs_out, void *fields_out);
 
-/* Steps a4-a6: deposit, node fields, then interpolation to every parcel. out (device,
+/* Steps a4-a6: deposit, node fields, then interpolation to every parcel (Sec. 3.1: the solids
+ * fraction at a parcel is interpolated from the mesh with the same weights the deposit uses;
+ * Eq. 4 needs grad p and grad tau at the parcel). out (device,
  * 10*np values in the parcel precision, back to back): eps_s, u_g[3], grad p[3],
  * grad tau[3] (the exact gradient of the trilinear interpolant of the node stresses). */
 mppic_status mppic_interp(mppic_handle *h, const mppic_parcels *parcels, const mppic_gas *gas,
@@ -163,7 +172,8 @@ mppic_status mppic_set_params(mppic_handle *h, double drag_mult, double dscale, 
  * every = 0 switches checkpointing off. */
 mppic_status mppic_checkpoint(mppic_handle *h, int every);
 
-/* Reverse mode, part 2: the gradient of L = a <dP> + b <H> over the steps of the last
+/* Reverse mode, part 2. The paper has no counterpart: it differentiates nothing. This is the
+ * differentiation form added to the method: the gradient of L = a <dP> + b <H> over the steps of the last
  * checkpointed mppic_step call, where <.> is the average over its steps of the objectives
  * that call returned, with respect to (drag multiplier C, diameter scale s_d, inflow
  * velocity u_in). dL_d_dP_H (host, 2 doubles) = (a, b); grad_out (host, 3 doubles) receives

@@ -48,13 +48,20 @@ class OrcConfig(ctypes.Structure):
                 ("eps_cp", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("eps_g_min", ctypes.c_double), ("e_wall", ctypes.c_double),
                 ("drag_mult", ctypes.c_double), ("dscale", ctypes.c_double),
-                ("u_in", ctypes.c_double), ("dt", ctypes.c_double)]
+                ("u_in", ctypes.c_double), ("dt", ctypes.c_double),
+                ("drag_model", ctypes.c_int), ("coupling_iters", ctypes.c_int)]
+
+# drag closures: Wen-Yu, Syamlal-O'Brien, Gidaspow (switch at eps_g = 0.8), Gidaspow blend
+DRAG_MODELS = {"wen_yu": 0, "syamlal_obrien": 1, "gidaspow": 2, "gidaspow_blend": 3}
 
 
 def make_config(p: dict) -> OrcConfig:
     c = OrcConfig()
     for name, _ in OrcConfig._fields_:
         if name == "reserved0":
+            continue
+        if name in ("drag_model", "coupling_iters"):
+            setattr(c, name, int(p.get(name, 0)))
             continue
         v = p[name]
         if name in ("g", "gradp"):
@@ -88,6 +95,8 @@ def lib():
             L.orc_step_sample.argtypes = ([cp, ctypes.c_long] + [dp] * 8 + [dp] * 3
                                           + [ctypes.c_long, ctypes.POINTER(ctypes.c_long), dp, ip, dp])
             L.orc_step_sample.restype = ctypes.c_int
+            L.orc_couple.argtypes = [cp, ctypes.c_long] + [dp] * 24
+            L.orc_couple.restype = None
             _lib = L
     return _lib
 
@@ -161,7 +170,7 @@ def interp(p, x, y, z, eps_s, ug, tau, gradp=None):
 
 
 def drag(p, d, eps_s_p, ug_p, u, v, w):
-    """Wen-Yu acceleration coefficient D_p per parcel."""
+    """Acceleration coefficient D_p per parcel of the configured drag closure."""
     d, es = _f64(d), _f64(eps_s_p)
     ug = [_f64(ug_p[a]) for a in range(3)]
     u, v, w = _f64(u), _f64(v), _f64(w)
@@ -170,6 +179,28 @@ def drag(p, d, eps_s_p, ug_p, u, v, w):
     lib().orc_drag(ctypes.byref(c), d.size, _d(d), _d(es), _d(ug[0]), _d(ug[1]), _d(ug[2]),
                    _d(u), _d(v), _d(w), _d(D))
     return D
+
+
+def couple(p, state: dict, U=(None, None, None), gradp=None):
+    """The coupling at the start of a step without moving the parcels: deposit, node fields
+    and, with p["coupling_iters"] = K > 0, the K gas iterations of implicit coupling.
+
+    Returns a dict with Vs, eps_s, ug (3, Nn) after the iterations, tau, and the drag sums
+    A, B (3, Nn) of the last gas iteration (zero when K = 0)."""
+    a = {k: _f64(state[k]) for k in ("x", "y", "z", "u", "v", "w", "d", "omega")}
+    nn = nnode(p)
+    out = {k: np.empty(nn) for k in ("Vs", "eps_s", "tau", "A")}
+    ug, B = np.empty((3, nn)), np.empty((3, nn))
+    U = [_f64(t) for t in U]
+    gps = [None] * 3 if gradp is None else [_f64(gradp[i]) for i in range(3)]
+    c = make_config(p)
+    lib().orc_couple(ctypes.byref(c), a["x"].size, *[_d(a[k]) for k in
+                     ("x", "y", "z", "u", "v", "w", "d", "omega")],
+                     _d(U[0]), _d(U[1]), _d(U[2]), _d(gps[0]), _d(gps[1]), _d(gps[2]),
+                     _d(out["Vs"]), _d(out["eps_s"]), _d(ug[0]), _d(ug[1]), _d(ug[2]),
+                     _d(out["tau"]), _d(out["A"]), _d(B[0]), _d(B[1]), _d(B[2]))
+    out.update(ug=ug, B=B)
+    return out
 
 
 def step(p, state: dict, nsteps: int, U=(None, None, None), gradp=None, outputs=True):

@@ -14,13 +14,17 @@
 //   * tau_P = p_s eps_P^beta / max[eps_CP - eps_P, alpha (1 - eps_P)]
 //                                                            (Eq. 5)
 //   * F of Eq. 2 is the parcel force interpolated back to the mesh (Sec. 2.1)
+//   * explicit coupling deposits F once per time step; implicit coupling
+//     re-deposits it at the head of every gas (SIMPLE) iteration (Sec. 2.2.2)
 // The paper leaves drag, interpolation, reflection and the time integrator to
 // the MFiX theory guide. The readings used here (trilinear cloud-in-cell
-// weights on the node grid, Wen-Yu drag, semi-implicit drag with explicit
-// body and stress forces, specular walls at the parcel centre) are stated at
-// each function. Everything is evaluated in the obvious order, one parcel or
-// node at a time, in FP64, compiled with FMA contraction disabled so that the
-// binning formula is the plain IEEE product.
+// weights on the node grid; Wen-Yu, Syamlal-O'Brien, Gidaspow or blended
+// Gidaspow drag; semi-implicit drag with explicit body and stress forces;
+// specular walls at the parcel centre; the gas iteration of implicit coupling
+// reduced to the unsteady and drag terms of Eq. 2) are stated at each function.
+// Everything is evaluated in the obvious order, one parcel or node at a time,
+// in FP64, compiled with FMA contraction disabled so that the binning formula
+// is the plain IEEE product.
 //
 // The step is written once as a template over the scalar type: with S=double
 // it is the value oracle; with S=Dual<3> it carries forward-mode tangents with
@@ -49,6 +53,8 @@ typedef struct {
   double dscale;        // s_d: multiplies every parcel diameter
   double u_in;          // inflow velocity added to the z component of U at every node
   double dt;
+  int drag_model;       // 0 Wen-Yu, 1 Syamlal-O'Brien, 2 Gidaspow, 3 Gidaspow blend
+  int coupling_iters;   // 0 explicit coupling; K > 0 implicit coupling with K gas iterations
 } orc_config;
 
 }  // extern "C"
@@ -102,6 +108,13 @@ inline double sqrtz(double a) { return std::sqrt(a); }
 template <int N> inline Dual<N> sqrtz(const Dual<N>& a) {
   Dual<N> r(std::sqrt(a.v));
   double dd = (a.v == 0.0) ? 0.0 : 0.5 / r.v;
+  for (int i = 0; i < N; ++i) r.d[i] = dd * a.d[i];
+  return r; }
+// atan, for the blending function of the Gidaspow blend.
+inline double atanv(double a) { return std::atan(a); }
+template <int N> inline Dual<N> atanv(const Dual<N>& a) {
+  Dual<N> r(std::atan(a.v));
+  double dd = 1.0 / (1.0 + a.v * a.v);
   for (int i = 0; i < N; ++i) r.d[i] = dd * a.d[i];
   return r; }
 // max/min select one operand by value; the tangent follows the selected operand.
@@ -285,6 +298,73 @@ inline S wen_yu(const orc_config& c, const Params<S>& P, double d, const S& es, 
   return P.C * 0.75 * Cd_s * c.rho_g * powc(eg, -1.65) / (de * c.rho_p);
 }
 
+// Syamlal-O'Brien drag, the closure the paper's runs used (Sec. 2.1), as an acceleration
+// coefficient. With the particle Reynolds number Re = rho_g d |s| / mu and the terminal
+// velocity ratio of the suspension
+//   V_r = (A - 0.06 Re + sqrt((0.06 Re)^2 + 0.12 Re (2B - A) + A^2)) / 2,
+//   A = eps_g^4.14,  B = 0.8 eps_g^1.28 (eps_g <= 0.85) or eps_g^2.65 (eps_g > 0.85),
+// the drag coefficient is Dallavalle's at the reduced Reynolds number Re / V_r,
+//   C_D = (0.63 + 4.8 sqrt(V_r / Re))^2,
+// and the exchange coefficient beta = 3/4 C_D eps_s eps_g rho_g |s| / (V_r^2 d) gives
+//   D = beta / (eps_s rho_p) = C 3/4 C_D eps_g rho_g |s| / (V_r^2 d rho_p).
+// C_D |s| = (0.63 sqrt|s| + 4.8 sqrt(V_r mu / (rho_g d)))^2 keeps zero slip finite.
+// V_r is evaluated in the equal form V_r = (A + (A^2 + 2r(2B - A)) / (sqrt(Q) + r)) / 2,
+// r = 0.06 Re, Q = r^2 + 2r(2B - A) + A^2 (sqrt(Q) - r rationalised), whose terms are all
+// positive (A < 2B for every voidage): the printed form subtracts two numbers of size r and
+// loses digits as Re grows. eps_g is floored at eps_g_min as for Wen-Yu (reading).
+template <class S>
+inline S syamlal_obrien(const orc_config& c, const Params<S>& P, double d, const S& es,
+                        const S s[3]) {
+  S eg = maxv(1.0 - es, S(c.eps_g_min));
+  S de = P.sd * d;
+  S smag = sqrtz(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+  S Re = c.rho_g * de * smag / c.mu_g;
+  S A = powc(eg, 4.14);
+  S B = val(eg) <= 0.85 ? 0.8 * powc(eg, 1.28) : powc(eg, 2.65);
+  S r = 0.06 * Re;
+  S t = A * A + 2.0 * r * (2.0 * B - A);
+  S Vr = 0.5 * (A + t / (sqrtz(r * r + t) + r));
+  S root = 0.63 * sqrtz(smag) + 4.8 * sqrtz(Vr * c.mu_g / (c.rho_g * de));
+  S Cd_s = root * root;  // C_D * |s|
+  return P.C * 0.75 * Cd_s * eg * c.rho_g / (Vr * Vr * de * c.rho_p);
+}
+
+// Ergun's dense-bed exchange coefficient beta = 150 eps_s^2 mu / (eps_g d^2) +
+// 1.75 rho_g eps_s |s| / d as an acceleration coefficient D = beta / (eps_s rho_p), with
+// eps_s = 1 - eps_g of the floored voidage (reading).
+template <class S>
+inline S ergun(const orc_config& c, const Params<S>& P, double d, const S& es, const S s[3]) {
+  S eg = maxv(1.0 - es, S(c.eps_g_min));
+  S esf = 1.0 - eg;
+  S de = P.sd * d;
+  S smag = sqrtz(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+  return P.C * (150.0 * esf * c.mu_g / (eg * de * de) + 1.75 * c.rho_g * smag / de) / c.rho_p;
+}
+
+// Gidaspow drag: Ergun below a voidage of 0.8, Wen-Yu at and above it. The blended form
+// (Lu and Gidaspow) weights the two smoothly instead:
+//   phi = atan(150 * 1.75 (0.2 - eps_s)) / pi + 1/2,   D = (1 - phi) D_Ergun + phi D_WenYu,
+// so dilute suspensions take Wen-Yu and dense beds Ergun.
+template <class S>
+inline S gidaspow(const orc_config& c, const Params<S>& P, double d, const S& es, const S s[3],
+                  bool blend) {
+  S eg = maxv(1.0 - es, S(c.eps_g_min));
+  if (!blend) return val(eg) < 0.8 ? ergun(c, P, d, es, s) : wen_yu(c, P, d, es, s);
+  S phi = atanv(150.0 * 1.75 * (0.2 - (1.0 - eg))) / M_PI + 0.5;
+  return (1.0 - phi) * ergun(c, P, d, es, s) + phi * wen_yu(c, P, d, es, s);
+}
+
+// The configured drag closure.
+template <class S>
+inline S drag_coef(const orc_config& c, const Params<S>& P, double d, const S& es, const S s[3]) {
+  switch (c.drag_model) {
+    case 1: return syamlal_obrien(c, P, d, es, s);
+    case 2: return gidaspow(c, P, d, es, s, false);
+    case 3: return gidaspow(c, P, d, es, s, true);
+    default: return wen_yu(c, P, d, es, s);
+  }
+}
+
 // Specular reflection at the planes 0 and L, applied to the parcel centre.
 // Returns false if the parcel is still outside after one reflection.
 template <class S>
@@ -300,18 +380,89 @@ struct StepOut {
   S dP, H;
 };
 
-// One explicit coupling step (Sec. 2.2.2: parcel-to-fluid coupling once, then
-// the parcel update). Positions/velocities are advanced in place.
+// Drag sums of F (Eq. 2) for the parcels at rest in their current state, against the node
+// gas velocity ug: per parcel the interpolated fields, the drag coefficient D and
+// f = rho_p V D; A = sum_p f W, B = sum_p f u_P W. The parcels do not move.
+template <class S>
+void drag_sums(const orc_config& c, const Grid& G, const Params<S>& P, long np, const S* x,
+               const S* y, const S* z, const S* u, const S* v, const S* w, const double* d,
+               const double* om, const std::vector<S>& eps_s, const std::vector<S>& ug,
+               const std::vector<S>& tau, const double* const GP[3], std::vector<S>& A,
+               std::vector<S>& B) {
+  A.assign(G.nnode, S(0.0));
+  B.assign(3 * G.nnode, S(0.0));
+  Stencil<S> st;
+  Interp<S> I;
+  for (long p = 0; p < np; ++p) {
+    stencil(G, x[p], y[p], z[p], st);
+    interp(c, st, eps_s, ug, tau, GP, I);
+    S up[3] = {u[p], v[p], w[p]};
+    S s[3] = {I.ug[0] - up[0], I.ug[1] - up[1], I.ug[2] - up[2]};
+    S f = c.rho_p * parcel_volume(d[p], om[p], P.sd) * drag_coef(c, P, d[p], I.es, s);
+    for (int q = 0; q < 8; ++q) {
+      long n = st.nodes[q];
+      A[n] += f * st.W[q];
+      for (int a = 0; a < 3; ++a) B[3 * n + a] += (f * up[a]) * st.W[q];
+    }
+  }
+}
+
+// The gas iteration of implicit coupling (reading of Sec. 2.2.2 with the gas side reduced to
+// the unsteady and interphase terms of Eq. 2): per node, backward Euler in the gas velocity
+// with the drag force per node volume F = (A u_g - B) / V_n taken implicitly,
+//   eps_g rho_g V_n (u_g' - u_g0) / dt = -(A u_g' - B)
+//   =>  u_g' = (m u_g0 + B) / (m + A),   m = rho_g eps_g V_n / dt,
+// where u_g0 = U / max(eps_g, eps_g_min) is the gas velocity of the time step's start and
+// eps_g the floored voidage of the node.
+template <class S>
+void gas_update(const orc_config& c, const Grid& G, const Params<S>& P, const std::vector<S>& eps_s,
+                const double* const U[3], const std::vector<S>& A, const std::vector<S>& B,
+                std::vector<S>& ug) {
+  for (int k = 0; k <= G.n[2]; ++k)
+    for (int j = 0; j <= G.n[1]; ++j)
+      for (int i = 0; i <= G.n[0]; ++i) {
+        long n = G.node(i, j, k);
+        S egc = maxv(1.0 - eps_s[n], S(c.eps_g_min));
+        S m = c.rho_g * egc * G.node_volume(i, j, k) / c.dt;
+        for (int a = 0; a < 3; ++a) {
+          S Ua = S(U[a] ? U[a][n] : 0.0);
+          if (a == 2) Ua = Ua + P.uin;
+          S u0 = Ua / egc;
+          ug[3 * n + a] = (m * u0 + B[3 * n + a]) / (m + A[n]);
+        }
+      }
+}
+
+// Node fields of a time step's start and, with implicit coupling, the K gas iterations:
+// each re-deposits the drag sums against the current gas velocity and updates it.
+template <class S>
+void coupling(const orc_config& c, const Grid& G, const Params<S>& P, long np, const S* x,
+              const S* y, const S* z, const S* u, const S* v, const S* w, const double* d,
+              const double* om, const double* const U[3], const double* const GP[3],
+              std::vector<S>& Vs, std::vector<S>& eps_s, std::vector<S>& ug, std::vector<S>& tau,
+              std::vector<S>& A, std::vector<S>& B) {
+  // 1-2: bin and deposit the solids volume at the current positions.
+  deposit_volume(G, P, np, x, y, z, d, om, Vs);
+  // 3: node fields.
+  node_fields(c, G, P, Vs, U, eps_s, ug, tau);
+  // implicit coupling: F again at the head of every gas iteration
+  for (int m = 0; m < c.coupling_iters; ++m) {
+    drag_sums(c, G, P, np, x, y, z, u, v, w, d, om, eps_s, ug, tau, GP, A, B);
+    gas_update(c, G, P, eps_s, U, A, B, ug);
+  }
+}
+
+// One coupling step (Sec. 2.2.2): the parcel-to-fluid coupling (once with explicit
+// coupling; at the head of every gas iteration with implicit coupling), then the parcel
+// update against the last gas velocity, depositing the drag sums F of that update.
+// Positions/velocities are advanced in place.
 // Returns 0, or 4 if a parcel left the box or a value became non-finite.
 template <class S>
 int step_once(const orc_config& c, const Grid& G, const Params<S>& P, long np, S* x, S* y, S* z,
               S* u, S* v, S* w, const double* d, const double* om, int* cell,
               const double* const U[3], const double* const GP[3], StepOut<S>& out) {
-  // 1-2: bin and deposit the solids volume at the current positions.
-  deposit_volume(G, P, np, x, y, z, d, om, out.Vs);
-  // 3: node fields.
   std::vector<S> eps_s, ug, tau;
-  node_fields(c, G, P, out.Vs, U, eps_s, ug, tau);
+  coupling(c, G, P, np, x, y, z, u, v, w, d, om, U, GP, out.Vs, eps_s, ug, tau, out.A, out.B);
   // 4: per parcel interpolation, drag, drag sums, objectives, push, walls.
   out.A.assign(G.nnode, S(0.0));
   out.B.assign(3 * G.nnode, S(0.0));
@@ -324,7 +475,7 @@ int step_once(const orc_config& c, const Grid& G, const Params<S>& P, long np, S
     interp(c, st, eps_s, ug, tau, GP, I);
     S up[3] = {u[p], v[p], w[p]};
     S s[3] = {I.ug[0] - up[0], I.ug[1] - up[1], I.ug[2] - up[2]};
-    S D = wen_yu(c, P, d[p], I.es, s);
+    S D = drag_coef(c, P, d[p], I.es, s);
     S V = parcel_volume(d[p], om[p], P.sd);
     // Drag sums for F of Eq. 2 (pre-push state): A = sum f W, B = sum f u_P W.
     S f = c.rho_p * V * D;
@@ -433,14 +584,45 @@ void orc_interp(const orc_config* c, long np, const double* x, const double* y, 
   }
 }
 
-// Per-parcel drag coefficient D_p (Wen-Yu) for given interpolated eps_s, u_g.
+// Per-parcel drag coefficient D_p (the configured closure) for given interpolated eps_s, u_g.
 void orc_drag(const orc_config* c, long np, const double* d, const double* eps_s_p,
               const double* ugx, const double* ugy, const double* ugz, const double* u,
               const double* v, const double* w, double* D) {
   Params<double> P{c->drag_mult, c->dscale, c->u_in};
   for (long p = 0; p < np; ++p) {
     double s[3] = {ugx[p] - u[p], ugy[p] - v[p], ugz[p] - w[p]};
-    D[p] = wen_yu(*c, P, d[p], eps_s_p[p], s);
+    D[p] = drag_coef(*c, P, d[p], eps_s_p[p], s);
+  }
+}
+
+// The coupling at the start of a time step, without moving the parcels: the deposit, the
+// node fields and (with coupling_iters = K > 0) the K gas iterations of implicit coupling.
+// Outputs (each may be NULL): Vs, eps_s, the node gas velocity after the iterations
+// (ugx, ugy, ugz), tau, and the drag sums of the last gas iteration (A, Bx, By, Bz; zero
+// when K = 0).
+void orc_couple(const orc_config* c, long np, const double* x, const double* y, const double* z,
+                const double* u, const double* v, const double* w, const double* d,
+                const double* om, const double* Ux, const double* Uy, const double* Uz,
+                const double* gpx, const double* gpy, const double* gpz, double* Vs_out,
+                double* es_out, double* ugx, double* ugy, double* ugz, double* tau_out,
+                double* A_out, double* Bx, double* By, double* Bz) {
+  Grid G(*c);
+  Params<double> P{c->drag_mult, c->dscale, c->u_in};
+  std::vector<double> Vs, eps_s, ug, tau, A(G.nnode, 0.0), B(3 * G.nnode, 0.0);
+  const double* U[3] = {Ux, Uy, Uz};
+  const double* GP[3] = {gpx, gpy, gpz};
+  coupling(*c, G, P, np, x, y, z, u, v, w, d, om, U, GP, Vs, eps_s, ug, tau, A, B);
+  for (long n = 0; n < G.nnode; ++n) {
+    if (Vs_out) Vs_out[n] = Vs[n];
+    if (es_out) es_out[n] = eps_s[n];
+    if (ugx) ugx[n] = ug[3 * n];
+    if (ugy) ugy[n] = ug[3 * n + 1];
+    if (ugz) ugz[n] = ug[3 * n + 2];
+    if (tau_out) tau_out[n] = tau[n];
+    if (A_out) A_out[n] = A[n];
+    if (Bx) Bx[n] = B[3 * n];
+    if (By) By[n] = B[3 * n + 1];
+    if (Bz) Bz[n] = B[3 * n + 2];
   }
 }
 
@@ -489,11 +671,10 @@ int orc_step_sample(const orc_config* c, long np, const double* x, const double*
                     double* fout) {
   Grid G(*c);
   Params<double> P{c->drag_mult, c->dscale, c->u_in};
-  std::vector<double> Vs, eps_s, ug, tau;
-  deposit_volume(G, P, np, x, y, z, d, om, Vs);
+  std::vector<double> Vs, eps_s, ug, tau, A, B;
   const double* U[3] = {Ux, Uy, Uz};
   const double* GP[3] = {nullptr, nullptr, nullptr};
-  node_fields(*c, G, P, Vs, U, eps_s, ug, tau);
+  coupling(*c, G, P, np, x, y, z, u, v, w, d, om, U, GP, Vs, eps_s, ug, tau, A, B);
   int status = 0;
   Stencil<double> st;
   Interp<double> I;
@@ -503,7 +684,7 @@ int orc_step_sample(const orc_config* c, long np, const double* x, const double*
     interp(*c, st, eps_s, ug, tau, GP, I);
     double up[3] = {u[p], v[p], w[p]};
     double s[3] = {I.ug[0] - up[0], I.ug[1] - up[1], I.ug[2] - up[2]};
-    double D = wen_yu(*c, P, d[p], I.es, s);
+    double D = drag_coef(*c, P, d[p], I.es, s);
     double V = parcel_volume(d[p], om[p], P.sd);
     fout[t] = c->rho_p * V * D;
     double pos[3] = {x[p], y[p], z[p]};

@@ -30,6 +30,8 @@ _BASE = dict(
     eps_g_min=0.3, e_wall=1.0,
     drag_mult=1.0, dscale=1.0,
     dt=1e-4,
+    drag_model=0,          # 0 Wen-Yu, 1 Syamlal-O'Brien, 2 Gidaspow, 3 Gidaspow blend
+    coupling_iters=0,      # 0 explicit coupling; K > 0 implicit with K gas iterations
 )
 
 

@@ -353,3 +353,211 @@ def test_step_sample_agrees_with_full_step():
     for a, k in enumerate(("x", "y", "z", "u", "v", "w")):
         np.testing.assert_array_equal(out[a], ref[k][sample])
     np.testing.assert_array_equal(cell, ex["cell"][sample])
+
+
+# ------------------------------------------------ branches pinned later on --
+
+def test_interp_reproduces_a_linear_node_pressure_gradient():
+    """The node pressure-gradient path of the interpolation: a linear grad p field given at
+    the nodes is reproduced exactly at every parcel, each component on its own axis."""
+    p = P(6, 5, 4, dx=0.02, dy=0.015, dz=0.01)
+    rng = np.random.default_rng(21)
+    L = np.array([6 * 0.02, 5 * 0.015, 4 * 0.01])
+    pos = rng.uniform(0, 1, (400, 3)) * L
+    X, Y, Z = _node_coords(p)
+    zero = np.zeros_like(X)
+    coef = np.array([[3.0, 1.0, -2.0, 0.5], [-7.0, 0.25, 4.0, -1.0], [11.0, -3.0, 0.0, 2.0]])
+    gp = [c[0] + c[1] * X + c[2] * Y + c[3] * Z for c in coef]
+    out = oracle.interp(p, pos[:, 0], pos[:, 1], pos[:, 2], zero, [zero] * 3, zero, gradp=gp)
+    for a in range(3):
+        expect = coef[a, 0] + pos @ coef[a, 1:]
+        np.testing.assert_allclose(out[4 + a], expect, rtol=1e-13, atol=1e-13)
+
+
+def test_drag_sums_partition_of_unity_every_component():
+    """Every component of the drag sums: sum_n (A u_g,n - B_n)_a equals sum_p f_p s_p,a, with
+    f_p and the slip s_p from the interpolation and drag functions (pinned above), for random
+    parcel velocities in all three directions and a non-uniform gas field."""
+    bed = synth.fourier_bed(n=4000, nx=8, ny=6, nz=12, nsteps=1)
+    synth.random_velocities(bed, 0.3, 13)
+    p = bed.params
+    st = bed.parcels
+    _, ex, status = oracle.step(p, st, 1, U=bed.U)
+    assert status == 0
+    Vs, A, B = ex["Vs"], ex["A"], ex["B"]
+    es, ug, tau = oracle.node_fields(p, Vs, U=bed.U)
+    I = oracle.interp(p, st["x"], st["y"], st["z"], es, ug, tau)
+    D = oracle.drag(p, st["d"], I[0], I[1:4], st["u"], st["v"], st["w"])
+    V = st["omega"] * math.pi / 6 * st["d"] ** 3
+    f = p["rho_p"] * V * D
+    for a, k in enumerate(("u", "v", "w")):
+        lhs = float(np.sum(A * ug[a] - B[a]))
+        rhs = float(np.sum(f * (I[1 + a] - st[k])))
+        scale = float(np.sum(np.abs(f * (I[1 + a] - st[k]))))
+        assert abs(lhs - rhs) <= 1e-12 * scale, (a, lhs, rhs)
+
+
+def test_drag_voidage_floor_substitutes_eps_g_min():
+    """Below eps_g_min the drag takes eps_g = eps_g_min: at eps_s = 0.8 and 0.95 (eps_g 0.2,
+    0.05) it equals the drag at eps_s = 0.75 (eps_g = 0.25 = eps_g_min, exact in binary), and
+    the unfloored drag at eps_g = 0.25 (a config whose floor is lower), for every drag law."""
+    for model in range(4):
+        p = P(2, 2, 2, eps_g_min=0.25, drag_model=model)
+        q = dict(p, eps_g_min=0.01)
+        n = 5
+        d = np.full(n, 150e-6)
+        ug = [np.zeros(n), np.zeros(n), np.linspace(0.1, 2.0, n)]
+        zero = np.zeros(n)
+        Dfloor = [oracle.drag(p, d, np.full(n, es), ug, zero, zero, zero) for es in (0.8, 0.95, 0.75)]
+        Dref = oracle.drag(q, d, np.full(n, 0.75), ug, zero, zero, zero)
+        np.testing.assert_array_equal(Dfloor[0], Dfloor[2])
+        np.testing.assert_array_equal(Dfloor[1], Dfloor[2])
+        np.testing.assert_array_equal(Dfloor[2], Dref)
+        Dabove = oracle.drag(p, d, np.full(n, 0.5), ug, zero, zero, zero)
+        assert np.all(Dabove != Dfloor[2])
+
+
+# ------------------------------------------------------- other drag laws --
+
+def _dallavalle_terminal_velocity(d, rho_p, rho_g, mu, g):
+    """Single-particle terminal velocity with Dallavalle's drag coefficient
+    C_D = (0.63 + 4.8 / sqrt(Re))^2: 3/4 C_D rho_g u^2 / (d rho_p) = g (1 - rho_g/rho_p)."""
+    target = g * (1 - rho_g / rho_p)
+
+    def accel(u):
+        re = rho_g * d * u / mu
+        cd = (0.63 + 4.8 / math.sqrt(re)) ** 2
+        return 0.75 * cd * rho_g * u * u / (d * rho_p)
+
+    lo, hi = 1e-9, 1e3
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if accel(mid) < target else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("d", [100e-6, 200e-6, 400e-6])
+def test_syamlal_obrien_single_particle_settles_at_dallavalle_velocity(d):
+    """In an unbounded dilute suspension (eps_g -> 1) the Syamlal-O'Brien velocity ratio is 1
+    and the drag is Dallavalle's: one parcel in still gas settles at that terminal velocity."""
+    dz = 1.0 if d < 300e-6 else 2.0      # room to settle for 15 s
+    p = P(1, 1, 40, dx=1.0, dy=1.0, dz=dz, rho_p=2500.0, Ps=0.0, u_in=0.0, dt=1e-2,
+          drag_model=1)
+    ut = _dallavalle_terminal_velocity(d, 2500.0, 1.2, 1.8e-5, 9.81)
+    st = dict(x=np.array([0.5]), y=np.array([0.5]), z=np.array([39.5 * dz]),
+              u=np.zeros(1), v=np.zeros(1), w=np.zeros(1), d=np.array([d]),
+              omega=np.array([1e-9]))
+    s, _, status = oracle.step(p, st, 1500)
+    assert status == 0
+    assert -s["w"][0] == pytest.approx(ut, rel=1e-9)
+
+
+@pytest.mark.parametrize("eps_g", [0.45, 0.7, 0.85, 0.9, 0.99])
+def test_syamlal_obrien_creeping_and_inertial_limits(eps_g):
+    """The velocity ratio V_r tends to A = eps_g^4.14 as Re -> 0 and to B (0.8 eps_g^1.28 up
+    to eps_g = 0.85, eps_g^2.65 above) as Re -> infinity, so D tends to
+    17.28 mu eps_g / (A d^2 rho_p) and to 0.297675 eps_g rho_g |s| / (B^2 d rho_p)."""
+    p = P(2, 2, 2, drag_model=1, eps_g_min=0.05)
+    d, mu, rho_g, rho_p = 1e-4, 1.8e-5, 1.2, 2500.0
+    A = eps_g ** 4.14
+    B = 0.8 * eps_g ** 1.28 if eps_g <= 0.85 else eps_g ** 2.65
+    one = np.ones(1)
+    zero = np.zeros(1)
+    for slip, expect in ((1e-16, 17.28 * mu * eps_g / (A * d * d * rho_p)),
+                         (1e18, 0.75 * 0.63 ** 2 * eps_g * rho_g * 1e18 / (B * B * d * rho_p))):
+        D = oracle.drag(p, d * one, (1 - eps_g) * one, [zero, zero, slip * one], zero, zero, zero)
+        assert D[0] == pytest.approx(expect, rel=2e-7), (slip, D[0], expect)
+
+
+@pytest.mark.parametrize("eps_g,U", [(0.45, 0.05), (0.5, 0.2), (0.6, 0.4), (0.75, 0.8)])
+def test_gidaspow_dense_bed_pressure_gradient_is_ergun(eps_g, U):
+    """A uniform lattice bed at rest below a voidage of 0.8 under Gidaspow drag: with the
+    steady, uniform gas momentum balance of Eq. 2 (0 = -eps_g grad p - F), the drag-borne
+    pressure gradient dP / (eps_g H) is Ergun's equation
+    150 mu U (1-eps)^2 / (eps^3 d^2) + 1.75 rho_g U^2 (1-eps) / (eps^3 d)."""
+    d, rho_p, mu, rho_g = 200e-6, 2500.0, 1.8e-5, 1.2
+    p = P(3, 3, 4, Ps=0.0, u_in=U, rho_p=rho_p, eps_g_min=0.05, drag_model=2)
+    x, y, z = _lattice(p, 2)
+    omega = (1 - eps_g) * 1e-6 / 8 / (math.pi / 6 * d ** 3)
+    st = dict(x=x, y=y, z=z, u=np.zeros_like(x), v=np.zeros_like(x), w=np.zeros_like(x),
+              d=np.full(x.size, d), omega=np.full(x.size, omega))
+    _, ex, status = oracle.step(p, st, 1)
+    assert status == 0
+    H = 4 * 0.01
+    ergun = (150 * mu * U * (1 - eps_g) ** 2 / (eps_g ** 3 * d * d)
+             + 1.75 * rho_g * U * U * (1 - eps_g) / (eps_g ** 3 * d))
+    assert ex["obj"][0, 0] / (eps_g * H) == pytest.approx(ergun, rel=1e-12)
+
+
+def test_gidaspow_switch_and_blend():
+    """Gidaspow takes Wen-Yu at and above eps_g = 0.8 and Ergun below; the blend weights the
+    two equally at eps_s = 0.2 (phi = 1/2) and lies between them in the dense range."""
+    n = 4
+    d = np.full(n, 180e-6)
+    ug = [np.zeros(n), np.full(n, 0.1), np.linspace(0.2, 1.5, n)]
+    zero = np.zeros(n)
+    q = {m: P(2, 2, 2, drag_model=m, eps_g_min=0.05) for m in range(4)}
+    D = lambda m, es: oracle.drag(q[m], d, np.full(n, es), ug, zero, zero, zero)
+    for es in (0.0, 0.1, 0.2):
+        np.testing.assert_array_equal(D(2, es), D(0, es))
+    for es in (0.2 + 1e-9, 0.3, 0.55):
+        assert np.all(D(2, es) != D(0, es))
+    ergun_at = D(2, 0.2 + 1e-12)              # the Ergun branch, continuous in eps_s
+    np.testing.assert_allclose(D(3, 0.2), 0.5 * (ergun_at + D(0, 0.2)), rtol=1e-9)
+    for es in (0.25, 0.4, 0.6):               # Gidaspow is Ergun here
+        b = D(3, es)
+        lo, hi = np.minimum(D(0, es), D(2, es)), np.maximum(D(0, es), D(2, es))
+        assert np.all(b >= lo * (1 - 1e-12)) and np.all(b <= hi * (1 + 1e-12))
+
+
+# ----------------------------------------------------- implicit coupling --
+
+def _moving_lattice(p, vel, per_axis=2, d=200e-6, eps_s=0.3):
+    x, y, z = _lattice(p, per_axis)
+    omega = eps_s * p["dx"] * p["dy"] * p["dz"] / per_axis ** 3 / (math.pi / 6 * d ** 3)
+    n = x.size
+    return dict(x=x, y=y, z=z, u=np.full(n, vel[0]), v=np.full(n, vel[1]), w=np.full(n, vel[2]),
+                d=np.full(n, d), omega=np.full(n, omega))
+
+
+def test_implicit_coupling_limits():
+    """The gas iteration of implicit coupling: with negligible gas inertia (dt -> infinity)
+    one iteration drags the node gas velocity to the f-weighted mean parcel velocity, which
+    for parcels all moving with v is v itself; with dt -> 0 the gas velocity stays U/eps_g;
+    with no iteration (explicit coupling) the node fields are those of the deposit alone."""
+    vel = (0.3, -0.2, 0.7)
+    base = P(3, 4, 5, u_in=0.4, Ps=0.0, eps_g_min=0.05)
+    st = _moving_lattice(base, vel)
+    explicit = oracle.couple(dict(base, coupling_iters=0), st)
+    es, ug0, _ = oracle.node_fields(base, explicit["Vs"])
+    np.testing.assert_array_equal(explicit["ug"], ug0)
+    assert np.all(explicit["A"] == 0) and np.all(explicit["B"] == 0)
+    heavy = oracle.couple(dict(base, coupling_iters=1, dt=1e12), st)
+    for a in range(3):
+        np.testing.assert_allclose(heavy["ug"][a], vel[a], rtol=1e-9, atol=1e-12)
+    light = oracle.couple(dict(base, coupling_iters=3, dt=1e-20), st)
+    np.testing.assert_allclose(light["ug"], ug0, rtol=1e-9, atol=1e-12)
+
+
+def test_implicit_coupling_uniform_bed_follows_the_scalar_recurrence():
+    """A uniform lattice bed at rest (every node at the same eps_s, f uniform): each gas
+    iteration is the scalar recurrence u' = m u0 / (m + rho_p eps_s D(u)) per unit volume,
+    m = rho_g eps_g / dt, with D from the drag function; K iterations of the oracle equal
+    K steps of the recurrence at every node, for every drag law."""
+    for model in range(4):
+        p = P(3, 3, 4, u_in=0.5, Ps=0.0, eps_g_min=0.05, dt=2e-3, drag_model=model)
+        st = _moving_lattice(p, (0.0, 0.0, 0.0), eps_s=0.35)
+        K = 4
+        out = oracle.couple(dict(p, coupling_iters=K), st)
+        es = 0.35
+        eg = 1 - es
+        u0 = 0.5 / eg
+        m = p["rho_g"] * eg / p["dt"]
+        u = u0
+        one, zero = np.ones(1), np.zeros(1)
+        for _ in range(K):
+            D = oracle.drag(p, 200e-6 * one, es * one, [zero, zero, u * one], zero, zero, zero)[0]
+            u = m * u0 / (m + p["rho_p"] * es * D)
+        np.testing.assert_allclose(out["eps_s"], es, rtol=1e-12)
+        np.testing.assert_allclose(out["ug"][2], u, rtol=1e-11)
+        np.testing.assert_allclose(out["ug"][0], 0.0, atol=1e-15)
