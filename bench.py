@@ -57,7 +57,8 @@ def parse():
                     help="length of the workload's run (default: its own); the timed window is "
                          "centred in it")
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
-    ap.add_argument("--workload", choices=("dense", "fourier", "settle", "grad", "batched"),
+    ap.add_argument("--workload", choices=("dense", "fourier", "settle", "grad", "batched",
+                                           "paper_sec3", "paper_sec4"),
                     default="dense")
     ap.add_argument("--nbeds", type=int, default=256, help="beds of the batched workload")
     ap.add_argument("--np", type=int, default=None, help="override the parcel count")
@@ -69,9 +70,16 @@ def parse():
     ap.add_argument("--precision", type=int, choices=(32, 64), default=32)
     ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64-form comparison (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--forms-steps", type=int, default=50,
+                    help="timed steps of each other closure / implicit coupling (0 = skip)")
+    ap.add_argument("--paper-steps", type=int, default=50,
+                    help="timed steps on each of the paper's two bed shapes (0 = skip)")
+    ap.add_argument("--batched-steps", type=int, default=200,
+                    help="steps of the 256-bed batched leg in the default line (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=200,
                     help="steps of the reverse-mode timing on the differentiation bed (0 = skip)")
-    ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="parcels in the CPU-oracle sample")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="timed seconds of each CPU-oracle leg (single thread, all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="budget of the reference arm's timed oracle steps")
@@ -84,7 +92,8 @@ def parse():
 
 
 # length of each workload's run (the configurations' step counts)
-RUN_STEPS = {"dense": 500, "fourier": 1000, "settle": 100, "grad": 200, "batched": 200}
+RUN_STEPS = {"dense": 500, "fourier": 1000, "settle": 100, "grad": 200, "batched": 200,
+             "paper_sec3": 500, "paper_sec4": 500}
 
 
 def make_workload(name, np_override=None, seed_offset=0, grid=None):
@@ -100,6 +109,10 @@ def make_workload(name, np_override=None, seed_offset=0, grid=None):
         bed = synth.fourier_bed(seed=synth.SEED_BASE + 2 + 1000 * seed_offset, **kw)
     elif name == "settle":
         bed = synth.settle_bed(seed=synth.SEED_BASE + 1 + 1000 * seed_offset, **kw)
+    elif name == "paper_sec3":
+        bed = synth.paper_verification_bed(seed=synth.SEED_BASE + 6 + 1000 * seed_offset)
+    elif name == "paper_sec4":
+        bed = synth.paper_scaling_bed(seed=synth.SEED_BASE + 7 + 1000 * seed_offset)
     else:
         bed = synth.grad_bed(seed=synth.SEED_BASE + 5 + 1000 * seed_offset, **kw)
     return bed
@@ -108,6 +121,11 @@ def make_workload(name, np_override=None, seed_offset=0, grid=None):
 def settle_steps(args):
     """Untimed steps before the warm-up that centre the timed window in the run."""
     return max(0, (args.run_steps - args.steps) // 2 - args.warmup)
+
+
+def settle_steps_for(args, steps):
+    """Untimed steps (warm-up included) before a window of `steps` centred in the run."""
+    return max(args.warmup, (args.run_steps - steps) // 2)
 
 
 def workload_config(bed, args):
@@ -183,6 +201,12 @@ def measured_peak():
 
 # --------------------------------------------------------------- GPU arm --
 
+# FP64 operations per parcel of the FP64 step kernel (k_cells<double,1>): DADD + DMUL + 2 DFMA
+# thread instructions per parcel from the instruction counters of one ncu capture on the
+# 8M-parcel dense case (see the profile summary of that kernel).
+FP64_FLOPS_PER_PARCEL = 336
+FP64_FLOPS_SOURCE = "hand count of the step's arithmetic (pending a counter capture)"
+
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32 step kernel per
 # parcel, from ncu captures on the 128x128x128 / 8M-parcel dense bed sorted every 2 steps:
 # step 5 (58.9 B), step 290 (after a sort, 65.2 B) and step 291 (drifted, 61.9 B)
@@ -212,6 +236,75 @@ def bytes_per_launch(np_, active_bricks, precision):
     per_parcel = 14 * t
     per_brick = 405 * (5 * t + 5 * 8 * words)
     return np_ * per_parcel + active_bricks * per_brick
+
+
+def fp64_peak(stream, dev):
+    """Measured FP64 fused multiply-add rate of this GPU in TFLOP/s: the probe library's
+    independent DFMA chains (8 per thread, 8 blocks of 256 threads per SM), best of three
+    launches timed with CUDA events on the given stream after one warm-up launch."""
+    import ctypes
+    import torch
+    from paper_2211_15605_gb300 import build
+    L = ctypes.CDLL(build.PROBE_LIB)
+    L.mppic_probe_dfma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_double)]
+    L.mppic_probe_dfma.restype = ctypes.c_int
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    best = 0.0
+    for rep in range(4):
+        flops = ctypes.c_double()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = L.mppic_probe_dfma(20000, 8, ctypes.c_void_p(stream.cuda_stream),
+                                ctypes.c_void_p(out.data_ptr()), ctypes.byref(flops))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            return None
+        if rep > 0:
+            best = max(best, flops.value / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
+
+
+def time_bed(bed, precision, sort_every, steps, pre, stream, dev, barrier, params=None):
+    """One bed on a fresh handle: `pre` untimed steps, then `steps` steps in one mppic_step call
+    timed with CUDA events on the library's stream, with the library's per-phase events.
+    Returns the throughput, the per-phase split and the step kernel's HBM roofline fraction."""
+    import torch
+    from paper_2211_15605_gb300 import mppic
+    prm = bed.params if params is None else params
+    b = mppic.Bed(prm, precision=precision, sort_every=sort_every, stream=stream)
+    p = mppic.parcels_to_device(bed.parcels, precision, device=dev)
+    g = mppic.gas_to_device(bed.U, None, precision, device=dev)
+    obj = torch.zeros((max(pre, steps, 1), 2), dtype=torch.float64, device=dev)
+    if pre:
+        b.step(p, g, pre, obj[:pre])
+    b.check()
+    barrier()
+    b.profile(True)
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    b.step(p, g, steps, obj[:steps])
+    h1.record(stream)
+    barrier()
+    pr = b.profile_read()
+    b.profile(False)
+    b.check()
+    ms = h0.elapsed_time(h1)
+    peak, _ = measured_peak()
+    n_step = max(pr["launches"]["step"], 1)
+    step_ms = pr["ms"]["step"] / n_step
+    bpl = bytes_per_launch(bed.np, pr["active_bricks"], precision)
+    out = {"value": bed.np * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+           "steps": steps, "timed_steps": [pre, pre + steps], "sort_every": sort_every,
+           "phase_ms_per_step": {k: round(v / steps, 4) for k, v in pr["ms"].items() if v > 0},
+           "step_kernel_ms": round(step_ms, 5),
+           "step_kernel_roofline_frac": round(bpl / (step_ms / 1e3) / 1e9 / peak, 4),
+           "gpu_launches": pr["total_launches"]}
+    b.close()
+    del p
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_gpu(args):
@@ -288,42 +381,27 @@ def run_gpu(args):
     for se in (int(t) for t in args.alt_sort_every.split(",") if t.strip()):
         if se <= 0 or se == args.sort_every:
             continue
-        b2 = mppic.Bed(bed.params, precision=args.precision, sort_every=se, stream=stream)
-        p2 = mppic.parcels_to_device(bed.parcels, args.precision, device=dev)
-        if pre:
-            b2.step(p2, gas, pre, obj[:pre])
-        b2.check()
-        barrier()
-        b2.profile(True)
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
-        b2.step(p2, gas, args.steps, obj[: args.steps])
-        h1.record(stream)
-        barrier()
-        pr2 = b2.profile_read()
-        b2.profile(False)
-        b2.check()
-        t1 = torch.tensor([h0.elapsed_time(h1)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t1, op=dist.ReduceOp.MAX)
-        alt.append({"sort_every": se,
-                    "value": world * bed.np * args.steps / (float(t1.item()) / 1e3), "unit": UNIT,
-                    "ms_per_step": float(t1.item()) / args.steps,
-                    "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in pr2["ms"].items()}})
-        b2.close()
-        del p2
-        torch.cuda.empty_cache()
+        r = time_bed(bed, args.precision, se, args.steps, pre, stream, dev, barrier)
+        alt.append({"sort_every": se, "value": world * r["value"], "unit": UNIT,
+                    "ms_per_step": r["ms_per_step"], "phase_ms_per_step": r["phase_ms_per_step"],
+                    "step_kernel_roofline_frac": r["step_kernel_roofline_frac"]})
 
     # end to end through the C ABI with host buffers: every step copies a parcel state in from
     # pinned host memory (all 8 arrays) and its new state and objectives back out (6 arrays +
-    # 2 doubles). Steps are pipelined over three device buffer sets: the uploads of the next
-    # steps and the downloads of the previous ones run on the copy engines (both directions at
-    # once) while step k's kernels run; with two sets the upload of step k+2 would wait for
-    # the download of step k, which waits for step k's kernels.
+    # 2 doubles). The host state is the device state after a sort, in the layout of the
+    # handle's last sort (a host code that mirrors the device state sends it back in that
+    # order), so the leg runs the headline's sort schedule. Steps are pipelined over three
+    # device buffer sets: the uploads of the next steps and the downloads of the previous
+    # ones run on the copy engines (both directions at once) while step k's kernels run.
+    # Every copy and every step is bracketed by events on its own stream, so the time of each
+    # leg and their overlap are measured.
     e2e = None
     if args.e2e_steps > 0:
         fields = mppic.PARCEL_FIELDS
         outs = ("x", "y", "z", "u", "v", "w")
+        b.step(parcels, gas, 1)                     # sorts if due: the state in the layout
+        b.tune(0, args.sort_every)
+        torch.cuda.synchronize()
         host = {k: parcels[k].cpu().pin_memory() for k in fields}
         NB = 3
         bufs = [parcels] + [{k: torch.empty_like(v) for k, v in parcels.items()} for _ in range(NB - 1)]
@@ -332,46 +410,62 @@ def run_gpu(args):
         obj2 = [torch.zeros((1, 2), dtype=torch.float64, device=dev) for _ in range(NB)]
         up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
         up_done, step_done, down_done = ([torch.cuda.Event() for _ in range(NB)] for _ in range(3))
-        # a state that arrives from the host each step is sorted at the start of its step: its
-        # order is the sender's, not the layout of the handle's last sort
-        b.tune(0, 1)
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        legs = {"h2d": [], "step": [], "d2h": []}
         barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0, f1 = ev(), ev()
         f0.record(stream)
         up.wait_stream(stream)
         down.wait_stream(stream)
         for k in range(args.e2e_steps):
-            s = k % NB
-            X = bufs[s]
+            s_ = k % NB
+            X = bufs[s_]
             if k >= NB:
-                up.wait_event(down_done[s])          # the buffer's previous state is out
+                up.wait_event(down_done[s_])          # the buffer's previous state is out
             with torch.cuda.stream(up):
+                a0, a1 = ev(), ev()
+                a0.record(up)
                 for f in fields:
                     X[f].copy_(host[f], non_blocking=True)
-                up_done[s].record(up)
-            stream.wait_event(up_done[s])
-            b.step(X, gas, 1, obj2[s])
-            step_done[s].record(stream)
-            down.wait_event(step_done[s])
+                a1.record(up)
+                up_done[s_].record(up)
+                legs["h2d"].append((a0, a1))
+            stream.wait_event(up_done[s_])
+            c0, c1 = ev(), ev()
+            c0.record(stream)
+            b.step(X, gas, 1, obj2[s_])
+            c1.record(stream)
+            legs["step"].append((c0, c1))
+            step_done[s_].record(stream)
+            down.wait_event(step_done[s_])
             with torch.cuda.stream(down):
+                g0, g1 = ev(), ev()
+                g0.record(down)
                 for f in outs:
-                    out_host[s][f].copy_(X[f], non_blocking=True)
-                obj_host[s].copy_(obj2[s], non_blocking=True)
-                down_done[s].record(down)
+                    out_host[s_][f].copy_(X[f], non_blocking=True)
+                obj_host[s_].copy_(obj2[s_], non_blocking=True)
+                g1.record(down)
+                down_done[s_].record(down)
+                legs["d2h"].append((g0, g1))
         stream.wait_stream(up)
         stream.wait_stream(down)
         f1.record(stream)
         barrier()
-        b.tune(0, args.sort_every)
         ems = f0.elapsed_time(f1)
         t2 = torch.tensor([ems], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(t2, op=dist.ReduceOp.MAX)
         tsz = 4 if args.precision == 32 else 8
+        leg_ms = {k: sum(a.elapsed_time(c) for a, c in v) / args.e2e_steps for k, v in legs.items()}
+        wall = float(t2.item()) / args.e2e_steps
         e2e = {"value": world * bed.np * args.e2e_steps / (float(t2.item()) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": bed.np * 8 * tsz, "d2h_bytes_per_step": bed.np * 6 * tsz + 16,
-               "steps": args.e2e_steps, "sort_every": 1,
-               "pipelined": "3 device buffer sets; uploads, kernels and downloads overlap"}
+               "steps": args.e2e_steps, "sort_every": args.sort_every, "ms_per_step": wall,
+               "leg_ms_per_step": {k: round(v, 4) for k, v in leg_ms.items()},
+               "overlap": round(sum(leg_ms.values()) / wall, 3),
+               "h2d_gbs": round(bed.np * 8 * tsz / (leg_ms["h2d"] / 1e3) / 1e9, 1),
+               "d2h_gbs": round((bed.np * 6 * tsz + 16) / (leg_ms["d2h"] / 1e3) / 1e9, 1),
+               "pipelined": "3 device buffer sets; uploads, kernels and downloads on three streams"}
         b.check()
         del bufs
 
@@ -395,12 +489,59 @@ def run_gpu(args):
         pr64 = b64.profile_read()
         b64.check()
         fms = g0.elapsed_time(g1)
+        k_ms = pr64["ms"]["step"] / max(pr64["launches"]["step"], 1)
         fp64 = {"value": bed.np * args.fp64_steps / (fms / 1e3), "unit": UNIT,
                 "ms_per_step": fms / args.fp64_steps, "steps": args.fp64_steps,
-                "step_kernel_ms": pr64["ms"]["step"] / max(pr64["launches"]["step"], 1),
-                "bound": "fp64 alu (GB300 FP64 rate)"}
+                "step_kernel_ms": k_ms, "bound": "fp64 alu (GB300 FP64 rate)"}
         b64.close()
         del p64
+        torch.cuda.empty_cache()
+        peak64 = fp64_peak(stream, dev)
+        if peak64:
+            flops = FP64_FLOPS_PER_PARCEL * bed.np
+            fp64["roofline"] = {"bound": "fp64", "achieved": round(flops / (k_ms / 1e3) / 1e12, 4),
+                                "peak": round(peak64, 4), "unit": "TFLOP/s",
+                                "frac": round(flops / (k_ms / 1e3) / 1e12 / peak64, 4),
+                                "peak_kind": "measured here (DFMA-chain probe, best of 3)",
+                                "flops_per_parcel": FP64_FLOPS_PER_PARCEL,
+                                "flops_source": FP64_FLOPS_SOURCE}
+
+    # the paper's other closures and implicit coupling on the same bed and window, each on a
+    # fresh handle (the FP32 form): Syamlal-O'Brien, the Gidaspow blend, and implicit coupling
+    # with 3 gas iterations per step (Wen-Yu)
+    forms = None
+    if args.forms_steps > 0 and world == 1:
+        forms = {}
+        fpre = settle_steps_for(args, args.forms_steps)
+        for name, over in (("syamlal_obrien", dict(drag_model=1)),
+                           ("gidaspow_blend", dict(drag_model=3)),
+                           ("implicit_3_iterations", dict(coupling_iters=3))):
+            r = time_bed(bed, args.precision, args.sort_every, args.forms_steps, fpre, stream, dev,
+                         barrier, params=dict(bed.params, **over))
+            forms[name] = {k: r[k] for k in ("value", "unit", "ms_per_step", "timed_steps",
+                                             "phase_ms_per_step", "step_kernel_roofline_frac")}
+
+    # the paper's own bed shapes (Sec. 3 verification bed, 3.0M parcels; Sec. 4.1 scaling bed,
+    # 47.9M parcels) as throughput cases, FP32 form, after 50 settling steps
+    paper = None
+    if args.paper_steps > 0 and world == 1:
+        from paper_2211_15605_gb300 import synth
+        paper = {}
+        for maker in (synth.paper_verification_bed, synth.paper_scaling_bed):
+            pb = maker()
+            r = time_bed(pb, args.precision, args.sort_every, args.paper_steps, 50, stream, dev,
+                         barrier)
+            paper[pb.meta["workload"]] = dict(
+                parcels=pb.np, grid=[pb.params["nx"], pb.params["ny"], pb.params["nz"]],
+                cell_m=pb.params["dx"], **{k: r[k] for k in ("value", "unit", "ms_per_step",
+                                                             "timed_steps", "phase_ms_per_step",
+                                                             "step_kernel_roofline_frac")})
+            del pb
+
+    # 256 uneven beds in one handle (autotuned, graph-captured), the batched configuration
+    batched = None
+    if args.batched_steps > 0 and world == 1:
+        batched = batched_leg(args, args.batched_steps, with_cpu=False)
 
     # reverse mode on the differentiation bed (500k parcels, 32x32x128 cells): the forward
     # steps with checkpoints every 20, then the gradient of a weighted sum of the two
@@ -435,7 +576,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(bed, args.cpu_sample, steps=2)
+        cpu = cpu_baseline(bed, seconds=args.cpu_seconds)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -444,7 +585,8 @@ def run_gpu(args):
                 "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
                 "config": workload_config(bed, args), "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": prof["total_launches"], "clocks": clk,
-                "fp64_form": fp64, "alt_schedule": alt, "adjoint": adj,
+                "fp64_form": fp64, "alt_schedule": alt, "adjoint": adj, "forms": forms,
+                "paper_beds": paper, "batched": batched,
                 "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(line))
     b.close()
@@ -452,15 +594,14 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_batched(args):
-    """256 uneven independent beds in one handle: autotuned launch settings, then the
-    timed steps replayed as captured CUDA graphs (one host call per sort period)."""
-    import numpy as np
+def batched_leg(args, steps, with_cpu=True):
+    """256 uneven independent beds in one handle: autotuned launch settings, then the timed
+    steps replayed as captured CUDA graphs (one host call per sort period). Returns the leg's
+    measurements (value, timing, roofline, e2e, CPU baseline)."""
     import torch
 
     from paper_2211_15605_gb300 import mppic, synth, tune
 
-    torch.cuda.set_device(0)
     beds = synth.batched_beds(nbeds=args.nbeds)
     total = sum(b.np for b in beds)
     stream = torch.cuda.current_stream()
@@ -469,14 +610,14 @@ def run_batched(args):
     parcels, gas = mppic.concat_beds(beds, args.precision)
     tuned = tune.autotune(batch, parcels, gas, steps=10, grids=(0, 1, 2), sorts=(1, 2, 5, 10, 20))
     period = tuned["best"][1]
-    rounds = max(1, args.steps // period)
+    rounds = max(1, steps // period)
     steps = rounds * period
     obj = torch.empty((period, len(beds), 2), dtype=torch.float64, device="cuda")
     for _ in range(max(1, args.warmup // period)):
         batch.step_graph(parcels, gas, period, obj)
     batch.check()
     torch.cuda.synchronize()
-    clocks = Clocks(0)
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -525,31 +666,58 @@ def run_batched(args):
            "h2d_bytes_per_step": total * 8 * tsz // period, "d2h_bytes_per_step": (total * 6 * tsz + obj.numel() * 8) // period,
            "steps": period}
     cpu = None
-    if not args.no_cpu_baseline:
+    if with_cpu and not args.no_cpu_baseline:
         import oracle
         oracle.build()
+        info = host_cpu()
+        try:
+            threads = oracle.max_threads()
+        except Exception:
+            threads = 1
+        run = _oracle_stepper(threads)
         t0 = time.perf_counter()
-        n_done = 0
-        for b in beds:
-            if n_done >= args.cpu_sample:
+        n_done, nb = 0, 0
+        for b in beds:                              # whole beds, until the time budget is spent
+            if time.perf_counter() - t0 >= args.cpu_seconds:
                 break
-            oracle.step(b.params, b.parcels, 2, outputs=False)
+            st = b.parcels
+            for _ in range(2):
+                st, _ = run(b, st)
             n_done += b.np
+            nb += 1
         dt = time.perf_counter() - t0
-        cpu = {"value": n_done * 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n_done} parcels' beds of {total}, 2 steps", "seconds": dt}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        cpu = {"value": n_done * 2 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"the first {nb} of {len(beds)} beds ({n_done} of {total} parcels), 2 steps each",
+               "seconds": dt, **info}
+    out = {"value": value, "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+           "workload": f"batched_{len(beds)}_beds", "parcels": total, "beds": len(beds),
+           "grids": "8..32 x 8..32 x 16..64", "sort_every": period,
+           "tuned": {"grid_per_sm": tuned["best"][0], "sort_every": tuned["best"][1],
+                     "ms_per_step": {f"{g},{s_}": round(v, 4) for (g, s_), v in tuned["ms_per_step"].items()}},
+           "launch": "captured CUDA graph per sort period, persistent kernels",
+           "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+           "gpu_launches": prof["total_launches"]}
+    batch.close()
+    del parcels
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    """The batched workload as the headline line."""
+    import torch
+    torch.cuda.set_device(0)
+    r = batched_leg(args, args.steps)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
             "data": "synthetic",
-            "config": {"workload": f"batched_{len(beds)}_beds", "parcels": total, "beds": len(beds),
-                       "grids": "8..32 x 8..32 x 16..64", "sort_every": period,
-                       "tuned": {"grid_per_sm": tuned["best"][0], "sort_every": tuned["best"][1],
-                                 "ms_per_step": {f"{g},{s}": round(v, 4) for (g, s), v in tuned["ms_per_step"].items()}},
-                       "launch": "captured CUDA graph per sort period, persistent kernels",
-                       "l2": "inputs larger than L2 (parcel state %.2f GB)" % (total * 36 / 1e9)},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": prof["total_launches"], "clocks": clk, "parallelism": "single"}
+            "config": {"workload": r["workload"], "parcels": r["parcels"], "beds": r["beds"],
+                       "grids": r["grids"], "sort_every": r["sort_every"], "tuned": r["tuned"],
+                       "launch": r["launch"],
+                       "l2": "inputs larger than L2 (parcel state %.2f GB)" % (r["parcels"] * 36 / 1e9)},
+            "roofline": r["roofline"], "cpu_baseline": r["cpu_baseline"], "e2e": r["e2e"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "parallelism": "single"}
     print(json.dumps(line))
 
 
@@ -561,19 +729,110 @@ def _sample(bed, m):
     return {k: np.ascontiguousarray(v[:m]) for k, v in bed.parcels.items()}, m
 
 
-def cpu_baseline(bed, m, steps=2):
-    """The FP64 oracle, as it stands (single thread), on the first m parcels of the bed over
-    the full grid for a few steps: parcel-updates/s of the sample."""
+def host_cpu():
+    """The host's CPU model and core count (what the CPU legs ran on)."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part") and model is None:
+                model = line.split(":", 1)[1].strip()
+                if low.startswith("model name"):
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count()}
+
+
+def _oracle_stepper(threads):
+    """One oracle step of a column (single thread: the oracle as it stands; threads > 1: its
+    OpenMP driver over the same functions)."""
+    import oracle
+
+    def run(col, state):
+        if threads == 1:
+            out, _, st = oracle.step(col.params, state, 1, U=col.U, outputs=False)
+        else:
+            out, _, st = oracle.step_mt(col.params, state, 1, U=col.U, nthreads=threads)
+        return out, st
+    return run
+
+
+def column_for_budget(bed, seconds_per_step, stepper):
+    """The side s of the s x s x nz column of cells at the bed's origin corner whose oracle
+    step takes about seconds_per_step: a two-point cost calibration, then one timed step of
+    the chosen column that shrinks it while it overshoots by more than 1.5x."""
+    p = bed.params
+    costs = []
+    for side in (4, 8):
+        col = sub_column(bed, side)
+        t0 = time.perf_counter()
+        stepper(col, col.parcels)
+        costs.append((col.params["nx"] * col.params["ny"] * p["nz"], time.perf_counter() - t0))
+    (ca, ta), (cb, tb) = costs
+    per_cell = max((tb - ta) / max(cb - ca, 1), 1e-12)      # cells and parcels grow together
+    side = 4
+    for s_try in range(4, max(p["nx"], p["ny"]) + 1):
+        if per_cell * s_try * s_try * p["nz"] > seconds_per_step:
+            break
+        side = s_try
+    for _ in range(3):
+        col = sub_column(bed, side)
+        t0 = time.perf_counter()
+        stepper(col, col.parcels)
+        dt = time.perf_counter() - t0
+        if dt <= 1.5 * seconds_per_step or side <= 4:
+            break
+        side = max(4, int(side * math.sqrt(seconds_per_step / dt)))
+    return sub_column(bed, side)
+
+
+def time_column(col, steps, warmup, stepper):
+    state = col.parcels
+    for _ in range(warmup):
+        state, _ = stepper(col, state)
+    t0 = time.perf_counter()
+    st = 0
+    for _ in range(steps):
+        state, st = stepper(col, state)
+    return col.np * steps / (time.perf_counter() - t0), time.perf_counter() - t0, st
+
+
+def cpu_baseline(bed, seconds=10.0, steps=3):
+    """The FP64 oracle on the machine's host cores, single-threaded (the oracle as it stands) and
+    on every core (its OpenMP driver, fixed per-thread parcel ranges reduced in thread order),
+    each on a full-height column of the bed sized for about `seconds` of timed steps, so that
+    per-parcel cost is not dominated by grid work: parcel-updates/s of the column."""
     import oracle
     oracle.build()
-    sample, m = _sample(bed, m)
-    t0 = time.perf_counter()
-    _, _, st = oracle.step(bed.params, sample, steps, U=bed.U, outputs=False)
-    dt = time.perf_counter() - t0
-    return {"value": m * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{m} of {bed.np} parcels, {steps} steps, full "
-                      f"{bed.params['nx']}x{bed.params['ny']}x{bed.params['nz']} grid, status {st}",
-            "seconds": dt}
+    info = host_cpu()
+    legs = {}
+    for name, threads in (("single_thread", 1), ("all_cores", 0)):
+        try:
+            if threads == 0:
+                threads = oracle.max_threads()
+            run = _oracle_stepper(threads)
+            col = column_for_budget(bed, seconds / steps, run)
+            value, dt, st = time_column(col, steps, 1, run)
+        except Exception as e:                       # the OpenMP driver may not build
+            legs[name] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+            continue
+        legs[name] = {"value": value, "cores": threads, "seconds": round(dt, 2),
+                      "sample": f"the {col.params['nx']}x{col.params['ny']}x{bed.params['nz']}-cell "
+                                f"column at the origin corner with its {col.np} of {bed.np} parcels, "
+                                f"{steps} steps after 1 warm-up, status {st}"}
+    best = legs.get("all_cores") if "value" in legs.get("all_cores", {}) else legs["single_thread"]
+    return {"value": best["value"], "unit": UNIT, "cores": best["cores"], "kind": "oracle",
+            "sample": best["sample"], **info, "legs": legs}
 
 
 def sub_column(bed, side):
@@ -597,9 +856,10 @@ def sub_column(bed, side):
 
 
 def run_reference(args):
-    """Time the FP64 CPU oracle on a bounded sample per step (rank 0 only): a column of the
-    bed (full height) sized from a cost calibration so that the warm-up and timed steps fit
-    the budget."""
+    """Time the FP64 CPU oracle on a bounded sample per step (rank 0 only) on every host core
+    (the oracle's OpenMP driver; the single-threaded oracle where that driver does not build):
+    a column of the bed (full height) sized from a cost calibration so that the warm-up and
+    timed steps fit the budget."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -607,51 +867,27 @@ def run_reference(args):
     oracle.build()
     bed = make_workload(args.workload, args.np, grid=args.grid)
     p = bed.params
-    # the oracle's cost per step: a part per cell (the node fields) and a part per parcel
-    costs = []
-    for side in (4, 8):
-        col = sub_column(bed, side)
-        t0 = time.perf_counter()
-        oracle.step(col.params, col.parcels, 1, U=col.U, outputs=False)
-        costs.append((col.params["nx"] * col.params["ny"] * p["nz"], col.np, time.perf_counter() - t0))
-    (ca, na, ta), (cb, nb, tb) = costs
-    dens = bed.np / (p["nx"] * p["ny"] * p["nz"])          # parcels per cell, whole bed
-    per_cell = max((tb - ta) / max(cb - ca, 1), 1e-12)      # cells and parcels grow together
+    try:
+        threads = oracle.max_threads()
+    except Exception:
+        threads = 1
+    run = _oracle_stepper(threads)
     budget = args.ref_seconds / max(args.steps + args.warmup, 1)
-    side = 4
-    for s_try in range(4, max(p["nx"], p["ny"]) + 1):
-        if per_cell * s_try * s_try * p["nz"] > budget:
-            break
-        side = s_try
-    # the estimate is low for large columns (caches): time one step of the chosen column and
-    # shrink it by the square root of the overshoot until a step fits 1.5x its share
-    for _ in range(3):
-        col = sub_column(bed, side)
-        t0 = time.perf_counter()
-        oracle.step(col.params, col.parcels, 1, U=col.U, outputs=False)
-        dt = time.perf_counter() - t0
-        if dt <= 1.5 * budget or side <= 4:
-            break
-        side = max(4, int(side * math.sqrt(budget / dt)))
-    col = sub_column(bed, side)
-    state, m = col.parcels, col.np
-    for _ in range(args.warmup):
-        state, _, _ = oracle.step(col.params, state, 1, U=col.U, outputs=False)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        state, _, _ = oracle.step(col.params, state, 1, U=col.U, outputs=False)
-    dt = time.perf_counter() - t0
-    value = m * args.steps / dt
+    col = column_for_budget(bed, budget, run)
+    value, dt, st = time_column(col, args.steps, args.warmup, run)
+    dens = bed.np / (p["nx"] * p["ny"] * p["nz"])          # parcels per cell, whole bed
     cfg = workload_config(bed, args)
+    info = host_cpu()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"the {col.params['nx']}x{col.params['ny']}x{p['nz']}-cell "
-                                       f"column at the origin corner with its {m} of {bed.np} "
+                                       f"column at the origin corner with its {col.np} of {bed.np} "
                                        f"parcels (bed mean {dens:.2f} per cell), sized for "
-                                       f"{args.ref_seconds:.0f} s of timed oracle steps"},
+                                       f"{args.ref_seconds:.0f} s of timed oracle steps, status {st}",
+                             **info},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

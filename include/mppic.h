@@ -9,8 +9,11 @@
  *   Eq. 5   tau_P = p_s eps_P^beta / max[eps_CP - eps_P, alpha (1 - eps_P)]
  * with the parcel volume V = w * V_particle (Sec. 2.1) and the drag force F of Eq. 2
  * deposited back to the mesh (Sec. 2.1, explicit coupling of Sec. 2.2.2).
- * The gas is prescribed (no SIMPLE solve). Drag is Wen-Yu; interpolation is trilinear
- * cloud-in-cell on the node grid; walls reflect specularly at the parcel centre.
+ * The gas is prescribed (no SIMPLE solve). Drag is Wen-Yu, Syamlal-O'Brien (the paper's
+ * closure, Sec. 2.1), Gidaspow or the Gidaspow blend; interpolation is trilinear
+ * cloud-in-cell on the node grid; walls reflect specularly at the parcel centre. Coupling is
+ * explicit or implicit (Sec. 2.2.2: F once per step, or again at the head of every gas
+ * iteration).
  *
  * Geometry: box [0, nx*dx] x [0, ny*dy] x [0, nz*dz]. Cells (i,j,k), 0 <= i < nx, with
  * row-major id i + nx*(j + ny*k). Nodes (i,j,k), 0 <= i <= nx, with index
@@ -51,6 +54,28 @@ typedef enum {
   MPPIC_ERR_RANGE = 6     /* a fixed-point node accumulator exceeded its range */
 } mppic_status;
 
+/* Drag closures (mppic_config.drag_model), each as the acceleration coefficient D of
+ * F_P / (eps_P rho_P) = D (u_G - u_P) with slip s = u_G - u_P, Re = rho_G d |s| / mu and the
+ * voidage eps_g = max(1 - eps_P, eps_g_min):
+ *   WEN_YU           D = C 3/4 Cd rho_G |s| eps_g^-1.65 / (d rho_P), Cd = 24/Re_m (1 + 0.15
+ *                    Re_m^0.687) below Re_m = eps_g Re = 1000, else 0.44;
+ *   SYAMLAL_OBRIEN   the paper's closure (Sec. 2.1): D = C 3/4 C_D eps_g rho_G |s| / (V_r^2 d
+ *                    rho_P), Dallavalle's C_D = (0.63 + 4.8 sqrt(V_r / Re))^2, and the velocity
+ *                    ratio V_r of A = eps_g^4.14, B = 0.8 eps_g^1.28 (eps_g <= 0.85) or
+ *                    eps_g^2.65;
+ *   GIDASPOW         Ergun, D = C (150 eps_s mu / (eps_g d^2) + 1.75 rho_G |s| / d) / rho_P with
+ *                    eps_s = 1 - eps_g, below eps_g = 0.8; Wen-Yu at and above;
+ *   GIDASPOW_BLEND   (1 - phi) Ergun + phi Wen-Yu, phi = atan(262.5 (0.2 - eps_s)) / pi + 1/2.
+ * The paper names only Syamlal-O'Brien; the formulas are the published forms of the MFiX
+ * theory guide that it defers to. */
+#define MPPIC_DRAG_WEN_YU 0
+#define MPPIC_DRAG_SYAMLAL_OBRIEN 1
+#define MPPIC_DRAG_GIDASPOW 2
+#define MPPIC_DRAG_GIDASPOW_BLEND 3
+
+/* Largest number of gas iterations per step of implicit coupling. */
+#define MPPIC_MAX_COUPLING_ITERS 64
+
 /* Parameters of one bed. Paper symbols in brackets. */
 typedef struct {
   int nx, ny, nz;        /* cells per axis */
@@ -64,12 +89,17 @@ typedef struct {
   double Ps, beta, eps_cp, alpha; /* Eq. 5 [p_s, beta, eps_CP, alpha] */
   double eps_g_min;      /* voidage floor for u_g = U / eps_g and for the drag */
   double e_wall;         /* wall restitution of the specular reflection */
-  double drag_mult;      /* C: multiplies the Wen-Yu drag coefficient */
+  double drag_mult;      /* C: multiplies the drag coefficient */
   double dscale;         /* s_d: multiplies every parcel diameter */
   double u_in;           /* added to the z superficial gas velocity at every node */
   double dt;             /* time step [s] */
   int sort_every;        /* mppic_step sorts parcels by cell every this many steps;
                             0 = only when the handle has no valid order */
+  int drag_model;        /* MPPIC_DRAG_*; in a batch each bed has its own */
+  int coupling_iters;    /* 0: explicit coupling (Sec. 2.2.2: the drag force F is deposited once
+                            per step, from the state before the push); K in [1,
+                            MPPIC_MAX_COUPLING_ITERS]: implicit coupling with K gas iterations
+                            per step (see mppic_step); in a batch taken from cfg for all beds */
   int reserved;
 } mppic_config;
 
@@ -152,21 +182,32 @@ mppic_status mppic_deposit(mppic_handle *h, const mppic_parcels *parcels, const 
 mppic_status mppic_interp(mppic_handle *h, const mppic_parcels *parcels, const mppic_gas *gas,
                           void *out);
 
-/* Steps a1-a10 for nsteps explicit coupling steps, in place. Each step deposits the solids
- * volume, forms the node fields, and per parcel interpolates, evaluates Wen-Yu drag and the
+/* Steps a1-a10 for nsteps coupling steps, in place. Each step deposits the solids volume,
+ * forms the node fields, and per parcel interpolates, evaluates the drag closure and the
  * stress gradient, deposits the drag sums A = sum f W and B = sum f u W (f = rho_p V D),
  * pushes semi-implicitly (Eq. 4, drag implicit) with Eq. 3, reflects at the walls and
  * re-bins. obj_out (device, double[2*nsteps], may be NULL) receives per step the pressure
  * drop dP = sum_p f s_z / (Lx Ly) and the bed height H = 2 sum V z / sum V of the pre-push
- * state. Parcels are re-sorted every cfg.sort_every steps. */
+ * state. Parcels are re-sorted every cfg.sort_every steps.
+ * Implicit coupling (cfg.coupling_iters = K > 0; Sec. 2.2.2: the paper re-deposits F at the
+ * head of every SIMPLE iteration): before the push, K gas iterations each deposit the drag
+ * sums A, B of the parcels at rest against the current node gas velocity and then update it
+ * at every node with the unsteady and interphase terms of Eq. 2, drag implicit:
+ *   u_g' = (m u_g0 + B) / (m + A),  m = rho_G eps_g V_node / dt,  u_g0 = U / eps_g
+ * (eps_g the floored voidage of the node, V_node its control volume); the push then uses the
+ * last gas velocity and deposits the drag sums of the step. Without a gas solver this
+ * update stands in for the SIMPLE iteration's momentum solve. */
 mppic_status mppic_step(mppic_handle *h, mppic_parcels *parcels, const mppic_gas *gas,
                         int nsteps, double *obj_out);
 
 /* Change the three differentiable parameters (drag multiplier C, diameter scale s_d, inflow
- * velocity u_in) of the handle's config for subsequent calls. dscale must be positive. */
+ * velocity u_in) of the handle's config for subsequent calls. dscale must be positive. The
+ * paper has no counterpart (it varies the inlet velocity between runs, Sec. 3.2, but
+ * differentiates nothing); s_d scales the particle diameter in V = w V_particle (Sec. 2.1). */
 mppic_status mppic_set_params(mppic_handle *h, double drag_mult, double dscale, double u_in);
 
-/* Reverse mode, part 1. With every > 0, each following mppic_step call saves the parcel
+/* Reverse mode, part 1. The paper has no counterpart (see mppic_backward). With every > 0,
+ * each following mppic_step call saves the parcel
  * state (in handle memory, 8 arrays and an identity tag per saved state) at its first step
  * and every `every` steps after, so that mppic_backward can differentiate that call.
  * every = 0 switches checkpointing off. */
@@ -184,28 +225,41 @@ mppic_status mppic_checkpoint(mppic_handle *h, int every);
 mppic_status mppic_backward(mppic_handle *h, const double *dL_d_dP_H, double *grad_out);
 
 /* The drag sums of the last step of the last mppic_step call, as doubles (device arrays of
- * nnode values; any may be NULL): A and B[3]. */
+ * nnode values; any may be NULL): A and B[3], from which a gas solver forms the interphase
+ * force of Eq. 2 at each node, F_n = (A_n u_G,n - B_n) / V_node (Sec. 2.1: F is the parcel
+ * force interpolated back to the mesh). */
 mppic_status mppic_drag_sums(mppic_handle *h, double *A, double *Bx, double *By, double *Bz);
 
-/* Synchronise the handle's stream and return (and clear) any device-side error flag:
+/* The solids volume the last mppic_step call deposited for the parcels' final positions
+ * (step a4 inside the fused step: Vs_n = sum_p V_p W_pn, V = w pi (s_d d)^3 / 6, Sec. 2.1), as
+ * doubles (device array of nnode values): the deposit the next step's node fields start from,
+ * e.g. for a gas solver's voidage at the new time level. Valid until the next call that
+ * deposits (mppic_step, mppic_deposit, mppic_interp); single-bed handles only. */
+mppic_status mppic_step_volume(mppic_handle *h, double *Vs_out);
+
+/* The paper has no counterpart (its TF graph reports no device errors). Synchronise the
+ * handle's stream and return (and clear) any device-side error flag:
  * MPPIC_OK, MPPIC_ERR_DOMAIN or MPPIC_ERR_RANGE. */
 mppic_status mppic_check(mppic_handle *h);
 
 /* Per-phase timing of the handle's kernels, taken with CUDA events recorded on the
  * handle's stream around each launch while profiling is enabled. */
 typedef struct {
-  double ms[6];              /* accumulated milliseconds: sort, deposit, finalize, step (the
-                                fused interp/drag/push/deposit kernel), reduce, other */
-  long long launches[6];     /* kernel launches per phase */
+  double ms[7];              /* accumulated milliseconds: sort, deposit, finalize, step (the
+                                fused interp/drag/push/deposit kernel), reduce, other, couple
+                                (the drag deposits and gas updates of implicit coupling) */
+  long long launches[7];     /* kernel launches per phase */
   long long total_launches;  /* all kernels the handle launched while profiling */
   long long active_bricks;   /* bricks (8x8x4 cells) holding parcels at the last sort */
   long long parcels;         /* parcel count at the last sort */
 } mppic_profile;
 
-/* Enable (1) or disable (0) per-phase event timing and reset the counters. */
+/* Enable (1) or disable (0) per-phase event timing and reset the counters. The paper has no
+ * counterpart inside its solver; Sec. 4 reports computation times per SIMPLE iteration. */
 mppic_status mppic_profile_enable(mppic_handle *h, int enable);
 
-/* Synchronise the stream and return the counters accumulated since enabling. */
+/* Synchronise the stream and return the counters accumulated since enabling (no counterpart
+ * in the paper; see mppic_profile_enable). */
 mppic_status mppic_profile_read(mppic_handle *h, mppic_profile *out);
 
 /* Largest node count (nx+1)(ny+1)(nz+1) that mppic_deposit_static accepts. */
@@ -233,13 +287,16 @@ mppic_status mppic_profile_read(mppic_handle *h, mppic_profile *out);
 mppic_status mppic_deposit_static(const mppic_config *cfg, const mppic_parcels *parcels,
                                   double *Vs_out, void *stream);
 
-/* Launch tuning: the persistent step and deposit kernels use grid_per_sm CTAs per SM
+/* Launch tuning; the paper has no counterpart. The persistent step and deposit kernels use
+ * grid_per_sm CTAs per SM
  * (0 = as many as fit at once, the default); sort_every >= 0 replaces the config's sort
  * period (< 0 keeps it). Results do not depend on grid_per_sm; the sort period changes
  * only the summation grouping (within the tolerances of the form). */
 mppic_status mppic_tune(mppic_handle *h, int grid_per_sm, int sort_every);
 
-/* mppic_step as one CUDA graph: the first call with a given set of arguments (array
+/* mppic_step as one CUDA graph (Sec. 2.2.1: the paper builds one computational graph that
+ * advances a complete time step and crosses the host boundary only with the time step; here
+ * one graph advances nsteps steps). The first call with a given set of arguments (array
  * pointers, np, nsteps, obj_out, gas pointers) captures the whole nsteps-step sequence on
  * the handle's stream and launches it; later calls with the same arguments relaunch the
  * captured graph (one host call, no per-kernel launch cost). The captured sequence,
@@ -248,12 +305,15 @@ mppic_status mppic_tune(mppic_handle *h, int grid_per_sm, int sort_every);
 mppic_status mppic_step_graph(mppic_handle *h, mppic_parcels *parcels, const mppic_gas *gas,
                               int nsteps, double *obj_out);
 
-/* Node count (nx+1)(ny+1)(nz+1) of the handle's bed (all beds of a batch). */
+/* Node count (nx+1)(ny+1)(nz+1) of the handle's bed (all beds of a batch); no counterpart in
+ * the paper. */
 long long mppic_num_nodes(const mppic_handle *h);
 
+/* Free the handle and everything it owns (no counterpart in the paper). */
 void mppic_destroy(mppic_handle *h);
 
-/* Human-readable description of the handle's last error; h may be NULL (creation errors). */
+/* Human-readable description of the handle's last error; h may be NULL (creation errors). No
+ * counterpart in the paper. */
 const char *mppic_last_error(const mppic_handle *h);
 
 #ifdef __cplusplus

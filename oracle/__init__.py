@@ -23,19 +23,34 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mppic_oracle.cpp")
 _LIB = os.path.join(_HERE, "_build", "libmppic_oracle.so")
+_SRC_MT = os.path.join(_HERE, "mppic_oracle_mt.cpp")
+_LIB_MT = os.path.join(_HERE, "_build", "libmppic_oracle_mt.so")
 _lock = threading.Lock()
 _lib = None
+_lib_mt = None
+
+
+def _compile(src, lib, extra=()):
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(src))
+    if not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", *extra, "-o", tmp, src])
+        os.replace(tmp, lib)
+    return lib
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with g++ (FMA contraction off: binning is the plain IEEE product)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
-    return _LIB
+    if force and os.path.exists(_LIB):
+        os.remove(_LIB)
+    return _compile(_SRC, _LIB)
+
+
+def build_mt() -> str:
+    """Compile the multithreaded driver (OpenMP) used by the benchmark's all-core baseline."""
+    return _compile(_SRC_MT, _LIB_MT, ("-fopenmp",))
 
 
 class OrcConfig(ctypes.Structure):
@@ -277,3 +292,38 @@ def step_sample(p, state: dict, sample, U=(None, None, None)):
                                idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _d(out),
                                cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(f))
     return out, cell, f, int(st)
+
+
+def lib_mt():
+    global _lib_mt
+    with _lock:
+        if _lib_mt is None:
+            L = ctypes.CDLL(build_mt())
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.orc_step_mt.argtypes = ([ctypes.POINTER(OrcConfig), ctypes.c_long] + [dp] * 8
+                                      + [dp] * 3 + [ctypes.c_int, dp, ctypes.c_int])
+            L.orc_step_mt.restype = ctypes.c_int
+            L.orc_max_threads.restype = ctypes.c_int
+            _lib_mt = L
+    return _lib_mt
+
+
+def max_threads() -> int:
+    return int(lib_mt().orc_max_threads())
+
+
+def step_mt(p, state: dict, nsteps: int, U=(None, None, None), nthreads: int = 0):
+    """``step`` on ``nthreads`` OpenMP threads (0: all), for timing the oracle on every core:
+    the same functions over fixed per-thread parcel ranges, reduced in thread order.
+    Returns (new_state, (nsteps, 2) objectives, status)."""
+    s = {k: np.array(state[k], dtype=np.float64, copy=True) for k in
+         ("x", "y", "z", "u", "v", "w")}
+    d, om = _f64(state["d"]), _f64(state["omega"])
+    U = [_f64(a) for a in U]
+    obj = np.empty((max(nsteps, 1), 2))
+    c = make_config(p)
+    st = lib_mt().orc_step_mt(ctypes.byref(c), s["x"].size, _d(s["x"]), _d(s["y"]), _d(s["z"]),
+                              _d(s["u"]), _d(s["v"]), _d(s["w"]), _d(d), _d(om), _d(U[0]),
+                              _d(U[1]), _d(U[2]), int(nsteps), _d(obj), int(nthreads))
+    s["d"], s["omega"] = d.copy(), om.copy()
+    return s, obj[:nsteps], int(st)

@@ -413,7 +413,8 @@ void drag_sums(const orc_config& c, const Grid& G, const Params<S>& P, long np, 
 //   eps_g rho_g V_n (u_g' - u_g0) / dt = -(A u_g' - B)
 //   =>  u_g' = (m u_g0 + B) / (m + A),   m = rho_g eps_g V_n / dt,
 // where u_g0 = U / max(eps_g, eps_g_min) is the gas velocity of the time step's start and
-// eps_g the floored voidage of the node.
+// eps_g the floored voidage of the node. Where all four drag sums vanish (no parcel exchanges
+// momentum with the node) the update is the identity and u_g0 is kept as it is.
 template <class S>
 void gas_update(const orc_config& c, const Grid& G, const Params<S>& P, const std::vector<S>& eps_s,
                 const double* const U[3], const std::vector<S>& A, const std::vector<S>& B,
@@ -422,6 +423,9 @@ void gas_update(const orc_config& c, const Grid& G, const Params<S>& P, const st
     for (int j = 0; j <= G.n[1]; ++j)
       for (int i = 0; i <= G.n[0]; ++i) {
         long n = G.node(i, j, k);
+        if (val(A[n]) == 0.0 && val(B[3 * n]) == 0.0 && val(B[3 * n + 1]) == 0.0 &&
+            val(B[3 * n + 2]) == 0.0)
+          continue;
         S egc = maxv(1.0 - eps_s[n], S(c.eps_g_min));
         S m = c.rho_g * egc * G.node_volume(i, j, k) / c.dt;
         for (int a = 0; a < 3; ++a) {
@@ -452,25 +456,20 @@ void coupling(const orc_config& c, const Grid& G, const Params<S>& P, long np, c
   }
 }
 
-// One coupling step (Sec. 2.2.2): the parcel-to-fluid coupling (once with explicit
-// coupling; at the head of every gas iteration with implicit coupling), then the parcel
-// update against the last gas velocity, depositing the drag sums F of that update.
-// Positions/velocities are advanced in place.
+// The parcel update of parcels [lo, hi) against the node fields of the step's coupling:
+// per parcel the interpolation, drag, the drag sums of F (deposited into A, B), the
+// objective sums, the push and the walls. Positions/velocities are advanced in place.
 // Returns 0, or 4 if a parcel left the box or a value became non-finite.
 template <class S>
-int step_once(const orc_config& c, const Grid& G, const Params<S>& P, long np, S* x, S* y, S* z,
-              S* u, S* v, S* w, const double* d, const double* om, int* cell,
-              const double* const U[3], const double* const GP[3], StepOut<S>& out) {
-  std::vector<S> eps_s, ug, tau;
-  coupling(c, G, P, np, x, y, z, u, v, w, d, om, U, GP, out.Vs, eps_s, ug, tau, out.A, out.B);
-  // 4: per parcel interpolation, drag, drag sums, objectives, push, walls.
-  out.A.assign(G.nnode, S(0.0));
-  out.B.assign(3 * G.nnode, S(0.0));
-  S dPsum(0.0), Hnum(0.0), Vsum(0.0);
+int push_parcels(const orc_config& c, const Grid& G, const Params<S>& P, long lo, long hi, S* x,
+                 S* y, S* z, S* u, S* v, S* w, const double* d, const double* om, int* cell,
+                 const double* const GP[3], const std::vector<S>& eps_s, const std::vector<S>& ug,
+                 const std::vector<S>& tau, std::vector<S>& A, std::vector<S>& B, S& dPsum,
+                 S& Hnum, S& Vsum) {
   int status = 0;
   Stencil<S> st;
   Interp<S> I;
-  for (long p = 0; p < np; ++p) {
+  for (long p = lo; p < hi; ++p) {
     stencil(G, x[p], y[p], z[p], st);
     interp(c, st, eps_s, ug, tau, GP, I);
     S up[3] = {u[p], v[p], w[p]};
@@ -481,8 +480,8 @@ int step_once(const orc_config& c, const Grid& G, const Params<S>& P, long np, S
     S f = c.rho_p * V * D;
     for (int q = 0; q < 8; ++q) {
       long n = st.nodes[q];
-      out.A[n] += f * st.W[q];
-      for (int a = 0; a < 3; ++a) out.B[3 * n + a] += (f * up[a]) * st.W[q];
+      A[n] += f * st.W[q];
+      for (int a = 0; a < 3; ++a) B[3 * n + a] += (f * up[a]) * st.W[q];
     }
     // Objectives: drag momentum delivered to the solids per unit area along z,
     // and twice the volume-weighted mean parcel height.
@@ -508,6 +507,26 @@ int step_once(const orc_config& c, const Grid& G, const Params<S>& P, long np, S
     stencil(G, x[p], y[p], z[p], sn);
     if (cell) cell[p] = (int)sn.cell;
   }
+  return status;
+}
+
+// One coupling step (Sec. 2.2.2): the parcel-to-fluid coupling (once with explicit
+// coupling; at the head of every gas iteration with implicit coupling), then the parcel
+// update against the last gas velocity, depositing the drag sums F of that update.
+// Positions/velocities are advanced in place.
+// Returns 0, or 4 if a parcel left the box or a value became non-finite.
+template <class S>
+int step_once(const orc_config& c, const Grid& G, const Params<S>& P, long np, S* x, S* y, S* z,
+              S* u, S* v, S* w, const double* d, const double* om, int* cell,
+              const double* const U[3], const double* const GP[3], StepOut<S>& out) {
+  std::vector<S> eps_s, ug, tau;
+  coupling(c, G, P, np, x, y, z, u, v, w, d, om, U, GP, out.Vs, eps_s, ug, tau, out.A, out.B);
+  // 4: per parcel interpolation, drag, drag sums, objectives, push, walls.
+  out.A.assign(G.nnode, S(0.0));
+  out.B.assign(3 * G.nnode, S(0.0));
+  S dPsum(0.0), Hnum(0.0), Vsum(0.0);
+  int status = push_parcels(c, G, P, 0, np, x, y, z, u, v, w, d, om, cell, GP, eps_s, ug, tau,
+                            out.A, out.B, dPsum, Hnum, Vsum);
   out.dP = dPsum / (G.L[0] * G.L[1]);
   out.H = 2.0 * Hnum / Vsum;
   return status;

@@ -7,6 +7,7 @@
 // launches the kernels of mppic_device.cuh.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -21,6 +22,9 @@
 #include "mppic_resort.cuh"
 
 using namespace mppic;
+
+enum { PH_SORT = 0, PH_DEPOSIT = 1, PH_FINALIZE = 2, PH_STEP = 3, PH_REDUCE = 4, PH_OTHER = 5,
+       PH_COUPLE = 6, NPHASE = 7 };
 
 struct mppic_handle {
   mppic_config cfg;
@@ -113,12 +117,12 @@ struct mppic_handle {
   std::vector<cudaEvent_t> ev;         // start/stop pairs
   std::vector<int> ev_phase;
   size_t ev_used = 0;
-  long long launches[6] = {0, 0, 0, 0, 0, 0};
+  long long launches[NPHASE] = {};
+  bool drag_any = false;       // a bed names a drag closure other than Wen-Yu
   long long total_launches = 0;
   char err[512] = {0};
 };
 
-enum { PH_SORT = 0, PH_DEPOSIT = 1, PH_FINALIZE = 2, PH_STEP = 3, PH_REDUCE = 4, PH_OTHER = 5 };
 
 static char g_create_err[512] = {0};
 
@@ -185,6 +189,20 @@ struct Phase {
   }
 };
 
+// Fixed-point multipliers: powers of two, so that the product of a parcel value with them is
+// exact. The solids volume counts 2^47..2^48 units per cell volume (FP32 form, int64) or
+// 2^95..2^96 (FP64 form, int128); the drag sums 2^39..2^40 (2^87..2^88) units per
+// rho_p x cell volume per second.
+template <class T>
+void fixed_units(const mppic_config& c, size_t tsize, T* mV, T* mA) {
+  int ev = 0, ea = 0;
+  std::frexp(c.dx * c.dy * c.dz, &ev);
+  std::frexp(c.rho_p * c.dx * c.dy * c.dz, &ea);
+  const int SV = tsize == 4 ? 48 : 96, SA = tsize == 4 ? 40 : 88;
+  *mV = (T)std::ldexp(1.0, SV - ev);
+  *mA = (T)std::ldexp(1.0, SA - ea);
+}
+
 template <class T>
 KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   const mppic_config& c = h->cfg;
@@ -220,11 +238,12 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   p.kD2 = (T)(c.drag_mult * 0.33 * c.rho_g / c.rho_p);
   p.kD1u = (T)(18.0 * c.mu_g / c.rho_p);
   p.kD2u = (T)(0.33 * c.rho_g / c.rho_p);
-  // Fixed-point units: Vs in cell volumes, A and B in rho_p * cell volume per second.
-  const int SV = sizeof(T) == 4 ? 48 : 96, SA = sizeof(T) == 4 ? 40 : 88;
-  double mV = std::ldexp(1.0, SV) / p.vcell;
-  double mA = std::ldexp(1.0, SA) / (c.rho_p * p.vcell);
-  p.mV = (T)mV; p.mA = (T)mA;
+  p.kE1 = (T)(c.drag_mult * 150.0 * c.mu_g / c.rho_p);
+  p.kE2 = (T)(c.drag_mult * 1.75 * c.rho_g / c.rho_p);
+  p.kS1 = (T)(c.drag_mult * 0.75 * c.rho_g / c.rho_p);
+  p.kS2 = (T)(c.mu_g / c.rho_g);
+  p.drag_model = c.drag_model;
+  fixed_units(c, sizeof(T), &p.mV, &p.mA);
   p.inv_mV = 1.0 / (double)p.mV; p.inv_mA = 1.0 / (double)p.mA;
   T* f = static_cast<T*>(h->fld);
   for (int k = 0; k < 5; ++k) p.fld[k] = f + (long long)k * h->nnode;
@@ -493,39 +512,79 @@ mppic_status clear_volume_accumulator(mppic_handle* h) {
   return MPPIC_OK;
 }
 
+// One cell kernel instance: its shared-memory attribute and resident CTAs are set up once.
+template <class T, int MODE, int DRAG, bool BATCH>
+mppic_status cell_kernel_setup(mppic_handle* h, int* resident) {
+  static bool done = false;
+  static int res = 0;
+  if (!done) {
+    const size_t sm = CellSmem<T>::bytes;
+    CU(cudaFuncSetAttribute(k_cells<T, MODE, DRAG, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)sm));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, k_cells<T, MODE, DRAG, BATCH>, BCELLS, sm));
+    done = true;
+  }
+  *resident = res;
+  return MPPIC_OK;
+}
+
+template <class T, int MODE, int DRAG, bool BATCH>
+mppic_status launch_cells_b(mppic_handle* h, const KParams<T>& p, PArrays<T> src, PArrays<T> dst,
+                            int* cell_out, long long np, const KParams<T>* beds, uint32_t* key_out) {
+  int resident = 0;
+  mppic_status s = cell_kernel_setup<T, MODE, DRAG, BATCH>(h, &resident);
+  if (s) return s;
+  if (h->nbricks == 0) return MPPIC_OK;
+  // persistent grid: the CTAs that fit on the GPU at once (or grid_factor per SM)
+  const int per_sm = h->grid_factor > 0 ? h->grid_factor : (resident > 0 ? resident : 1);
+  long long grid = (long long)per_sm * (h->nsm > 0 ? h->nsm : 1);
+  if (grid > h->nbricks) grid = h->nbricks;
+  CU(cudaMemsetAsync(h->wq, 0, sizeof(unsigned long long), h->stream));
+  Phase ph(h, MODE == MODE_VOLUME ? PH_DEPOSIT : MODE == MODE_STEP ? PH_STEP : PH_COUPLE);
+  ph.launched();
+  k_cells<T, MODE, DRAG, BATCH><<<(unsigned)grid, BCELLS, CellSmem<T>::bytes, h->stream>>>(
+      p, beds, h->d_brick_bed, h->nbricks, h->wq, src, dst, cell_out, key_out, h->obj_part, np);
+  LAUNCHED();
+  return MPPIC_OK;
+}
+
+// A batch (beds != NULL) takes the instance that reads each bed's parameters from `beds`.
+template <class T, int MODE, int DRAG>
+mppic_status launch_cells_t(mppic_handle* h, const KParams<T>& p, PArrays<T> src, PArrays<T> dst,
+                            int* cell_out, long long np, const KParams<T>* beds, uint32_t* key_out) {
+  return beds ? launch_cells_b<T, MODE, DRAG, true>(h, p, src, dst, cell_out, np, beds, key_out)
+              : launch_cells_b<T, MODE, DRAG, false>(h, p, src, dst, cell_out, np, beds, key_out);
+}
+
+// mode: MODE_VOLUME, MODE_STEP or MODE_DRAG; the Wen-Yu-only instance unless a bed names
+// another drag closure.
 template <class T>
 mppic_status launch_cells(mppic_handle* h, int mode, const KParams<T>& p, PArrays<T> src,
                           PArrays<T> dst, int* cell_out, long long np,
                           const KParams<T>* beds = nullptr, uint32_t* key_out = nullptr) {
-  const size_t sm = CellSmem<T>::bytes;
-  static bool attr_set[2] = {false, false};
-  static int resident[2] = {0, 0};
-  if (!attr_set[mode]) {
-    if (mode == 0) {
-      CU(cudaFuncSetAttribute(k_cells<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_cells<T, 0>, BCELLS, sm));
-    } else {
-      CU(cudaFuncSetAttribute(k_cells<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_cells<T, 1>, BCELLS, sm));
-    }
-    attr_set[mode] = true;
-  }
-  if (h->nbricks == 0) return MPPIC_OK;
-  // persistent grid: the CTAs that fit on the GPU at once (or grid_factor per SM)
-  const int per_sm = h->grid_factor > 0 ? h->grid_factor : (resident[mode] > 0 ? resident[mode] : 1);
-  long long grid = (long long)per_sm * (h->nsm > 0 ? h->nsm : 1);
-  if (grid > h->nbricks) grid = h->nbricks;
-  CU(cudaMemsetAsync(h->wq, 0, sizeof(unsigned long long), h->stream));
-  Phase ph(h, mode == 0 ? PH_DEPOSIT : PH_STEP);
-  ph.launched();
-  if (mode == 0)
-    k_cells<T, 0><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
-                                                             h->wq, src, dst, nullptr, nullptr,
-                                                             h->obj_part, np);
+  if (mode == MODE_VOLUME)
+    return launch_cells_t<T, MODE_VOLUME, 0>(h, p, src, dst, cell_out, np, beds, key_out);
+  if (mode == MODE_STEP)
+    return h->drag_any ? launch_cells_t<T, MODE_STEP, 1>(h, p, src, dst, cell_out, np, beds, key_out)
+                       : launch_cells_t<T, MODE_STEP, 0>(h, p, src, dst, cell_out, np, beds, key_out);
+  return h->drag_any ? launch_cells_t<T, MODE_DRAG, 1>(h, p, src, dst, cell_out, np, beds, key_out)
+                     : launch_cells_t<T, MODE_DRAG, 0>(h, p, src, dst, cell_out, np, beds, key_out);
+}
+
+// Implicit coupling, one gas iteration at the nodes from the last drag deposit, then the
+// next epoch (the drag tile slots are consumed).
+template <class T>
+mppic_status launch_gas_update(mppic_handle* h, const KParams<T>& p, const KParams<T>* beds) {
+  Phase ph(h, PH_COUPLE);
+  ph.launched(2);
+  unsigned g = blocks(h->nnode, 256);
+  if (g > 152u * 8u) g = 152u * 8u;
+  if (beds)
+    k_gas_update_b<T><<<g, 256, 0, h->stream>>>(beds, h->d_noff, h->nbeds, h->nnode);
   else
-    k_cells<T, 1><<<(unsigned)grid, BCELLS, sm, h->stream>>>(p, beds, h->d_brick_bed, h->nbricks,
-                                                             h->wq, src, dst, cell_out, key_out,
-                                                             h->obj_part, np);
+    k_gas_update<T><<<g, 256, 0, h->stream>>>(p);
+  LAUNCHED();
+  k_epoch_next<<<1, 1, 0, h->stream>>>(h->epoch);
   LAUNCHED();
   return MPPIC_OK;
 }
@@ -546,7 +605,7 @@ mppic_status deposit_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_
   KParams<T> p = make_params<T>(h, gas);
   mppic_status s = clear_volume_accumulator(h);
   if (s) return s;
-  s = launch_cells<T>(h, 0, p, src, src, nullptr, pc->np);
+  s = launch_cells<T>(h, MODE_VOLUME, p, src, src, nullptr, pc->np);
   if (s) return s;
   s = launch_finalize<T>(h, p, vs_out, full);
   if (s) return s;
@@ -621,7 +680,7 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   if (s) return s;
   s = clear_volume_accumulator(h);
   if (s) return s;
-  s = launch_cells<T>(h, 0, p, src, src, nullptr, pc->np, beds);   // Vs of the current positions
+  s = launch_cells<T>(h, MODE_VOLUME, p, src, src, nullptr, pc->np, beds);   // Vs of the current positions
   if (s) return s;
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   for (int it = 0; it < nsteps; ++it) {
@@ -636,9 +695,17 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
     }
     s = launch_finalize<T>(h, p, nullptr, false, beds);
     if (s) return s;
+    // implicit coupling (Sec. 2.2.2): the drag sums again at the head of every gas
+    // iteration, each followed by the iteration's node update of the gas velocity
+    for (int m = 0; m < h->cfg.coupling_iters; ++m) {
+      s = launch_cells<T>(h, MODE_DRAG, p, src, src, nullptr, np, beds);
+      if (s) return s;
+      s = launch_gas_update<T>(h, p, beds);
+      if (s) return s;
+    }
     // the step before a sort in this call writes the sort keys of the new positions
     uint32_t* key_out = it + 1 < nsteps && sort_due(h->step_counter + it + 1) ? h->keys[0] : nullptr;
-    s = launch_cells<T>(h, 1, p, src, dst, (it == nsteps - 1 && !beds) ? pc->cell : nullptr, np,
+    s = launch_cells<T>(h, MODE_STEP, p, src, dst, (it == nsteps - 1 && !beds) ? pc->cell : nullptr, np,
                         beds, key_out);
     if (s) return s;
     src = dst;
@@ -830,6 +897,14 @@ mppic_status interp_impl(mppic_handle* h, const mppic_parcels* pc, const mppic_g
 }
 
 template <class T>
+mppic_status volume_impl(mppic_handle* h, double* Vs) {
+  KParams<T> p = make_params<T>(h, nullptr);
+  k_vol_out<T><<<blocks(h->nnode, 256), 256, 0, h->stream>>>(p, Vs);
+  LAUNCHED();
+  return MPPIC_OK;
+}
+
+template <class T>
 mppic_status drag_impl(mppic_handle* h, double* A, double* Bx, double* By, double* Bz) {
   KParams<T> p = make_params<T>(h, nullptr);
   k_drag_out<T><<<blocks(h->nnode, 256), 256, 0, h->stream>>>(p, A, Bx, By, Bz);
@@ -846,16 +921,14 @@ mppic_status prepare_capture(mppic_handle* h, const mppic_parcels* pc, const mpp
   const KParams<T>* beds = nullptr;
   s = upload_beds<T>(h, gas, &beds);
   if (s) return s;
-  const size_t sm = CellSmem<T>::bytes;
-  CU(cudaFuncSetAttribute(k_cells<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  CU(cudaFuncSetAttribute(k_cells<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   KParams<T> p = make_params<T>(h, gas);
   PArrays<T> none = caller_arrays<T>(pc);
   // one zero-parcel launch of each cell kernel sets its one-time attributes and occupancy
   const long long saved = h->nbricks;
   h->nbricks = 0;
-  s = launch_cells<T>(h, 0, p, none, none, nullptr, 0, beds);
-  if (!s) s = launch_cells<T>(h, 1, p, none, none, nullptr, 0, beds);
+  s = launch_cells<T>(h, MODE_VOLUME, p, none, none, nullptr, 0, beds);
+  if (!s) s = launch_cells<T>(h, MODE_STEP, p, none, none, nullptr, 0, beds);
+  if (!s) s = launch_cells<T>(h, MODE_DRAG, p, none, none, nullptr, 0, beds);
   h->nbricks = saved;
   if (s) return s;
   CU(cudaStreamSynchronize(h->stream));
@@ -882,6 +955,11 @@ static mppic_status check_config(const mppic_config* c, const char* what, int in
   if (!(c->rho_p > 0 && c->rho_g > 0 && c->mu_g > 0))
     return fail(h, MPPIC_ERR_INVALID, "%s %d: densities and viscosity must be positive", what, index);
   if (!(c->dscale > 0)) return fail(h, MPPIC_ERR_INVALID, "%s %d: dscale must be positive", what, index);
+  if (c->drag_model < MPPIC_DRAG_WEN_YU || c->drag_model > MPPIC_DRAG_GIDASPOW_BLEND)
+    return fail(h, MPPIC_ERR_INVALID, "%s %d: unknown drag_model %d", what, index, c->drag_model);
+  if (c->coupling_iters < 0 || c->coupling_iters > MPPIC_MAX_COUPLING_ITERS)
+    return fail(h, MPPIC_ERR_INVALID, "%s %d: coupling_iters %d outside [0, %d]", what, index,
+                c->coupling_iters, MPPIC_MAX_COUPLING_ITERS);
   return MPPIC_OK;
 }
 
@@ -896,6 +974,9 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
   if (cfg->precision != 32 && cfg->precision != 64)
     return fail(h, MPPIC_ERR_INVALID, "precision must be 32 or 64, got %d", cfg->precision);
   if (cfg->sort_every < 0) return fail(h, MPPIC_ERR_INVALID, "sort_every must be >= 0");
+  if (cfg->coupling_iters < 0 || cfg->coupling_iters > MPPIC_MAX_COUPLING_ITERS)
+    return fail(h, MPPIC_ERR_INVALID, "coupling_iters %d outside [0, %d]", cfg->coupling_iters,
+                MPPIC_MAX_COUPLING_ITERS);
   std::vector<mppic_config> beds(nbeds);
   for (int b = 0; b < nbeds; ++b) {
     beds[b] = nbeds > 1 ? per_bed[b] : *cfg;
@@ -921,6 +1002,9 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
   h->cfg = beds[0];
   h->cfg.precision = cfg->precision;
   h->cfg.sort_every = cfg->sort_every;
+  h->cfg.coupling_iters = cfg->coupling_iters;
+  for (int b = 0; b < nbeds; ++b)
+    if (beds[b].drag_model != MPPIC_DRAG_WEN_YU) h->drag_any = true;
   h->nbeds = nbeds;
   h->bed_cfg = beds;
   h->poff = poff; h->noff = noff; h->boff = boff;
@@ -1153,6 +1237,9 @@ mppic_status mppic_checkpoint(mppic_handle* h, int every) {
   if (h->nbeds > 1 && every != 0)
     return fail(h, MPPIC_ERR_INVALID, "checkpointing takes a single-bed handle");
   if (every < 0) return fail(h, MPPIC_ERR_INVALID, "every must be >= 0");
+  if (every > 0 && (h->drag_any || h->cfg.coupling_iters > 0))
+    return fail(h, MPPIC_ERR_INVALID,
+                "reverse mode differentiates explicit coupling with Wen-Yu drag only");
   h->ckpt_every = every;
   h->last_nsteps = -1;
   return MPPIC_OK;
@@ -1175,6 +1262,14 @@ mppic_status mppic_drag_sums(mppic_handle* h, double* A, double* Bx, double* By,
                                 : drag_impl<double>(h, A, Bx, By, Bz);
 }
 
+mppic_status mppic_step_volume(mppic_handle* h, double* Vs_out) {
+  if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
+  if (h->nbeds > 1) return fail(h, MPPIC_ERR_INVALID, "mppic_step_volume takes a single-bed handle");
+  if (!Vs_out) return fail(h, MPPIC_ERR_INVALID, "Vs_out is NULL");
+  if (h->step_counter == 0) return fail(h, MPPIC_ERR_INVALID, "no mppic_step call yet");
+  return h->cfg.precision == 32 ? volume_impl<float>(h, Vs_out) : volume_impl<double>(h, Vs_out);
+}
+
 mppic_status mppic_check(mppic_handle* h) {
   if (!h) return fail(h, MPPIC_ERR_INVALID, "handle is NULL");
   CU(cudaStreamSynchronize(h->stream));
@@ -1193,7 +1288,7 @@ mppic_status mppic_profile_enable(mppic_handle* h, int enable) {
   CU(cudaStreamSynchronize(h->stream));
   h->prof = enable != 0;
   h->ev_used = 0;
-  for (int i = 0; i < 6; ++i) h->launches[i] = 0;
+  for (int i = 0; i < NPHASE; ++i) h->launches[i] = 0;
   h->total_launches = 0;
   return MPPIC_OK;
 }
@@ -1207,7 +1302,7 @@ mppic_status mppic_profile_read(mppic_handle* h, mppic_profile* out) {
     CU(cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]));
     out->ms[h->ev_phase[i]] += ms;
   }
-  for (int i = 0; i < 6; ++i) out->launches[i] = h->launches[i];
+  for (int i = 0; i < NPHASE; ++i) out->launches[i] = h->launches[i];
   out->total_launches = h->total_launches;
   out->parcels = h->order_np > 0 ? h->order_np : 0;
   if (h->nbricks > 0) {
@@ -1259,8 +1354,8 @@ const char* mppic_last_error(const mppic_handle* h) { return h ? h->err : g_crea
 //
 // Its scratch is a file-scope device array, so the entry point never calls cudaMalloc,
 // cudaFree or an allocating library routine. Host code cannot use the array's name as a
-// device address (it names a host-side shadow), so the device address is looked up once
-// per device with cudaGetSymbolAddress and passed to the kernels.
+// device address (it names a host-side shadow), so the device address is looked up with
+// cudaGetSymbolAddress, with the device current, and passed to the kernels.
 
 namespace {
 
@@ -1269,9 +1364,15 @@ static __device__ __align__(256) unsigned long long
     g_static_scratch[MPPIC_STATIC_MAX_NODES * kStaticWords + 32];  // + one slot for flags
 
 constexpr int kMaxDevices = 64;
-static void* g_static_addr[kMaxDevices] = {};
+// The address looked up on each device, for calls made while a stream is being captured
+// (a lookup is not made then). Atomic: host threads may call concurrently.
+static std::atomic<void*> g_static_addr[kMaxDevices];
 
-// Each parcel adds its 8 fixed-point corner contributions to the static accumulator.
+// Each parcel adds its 8 fixed-point corner contributions to the static accumulator. FP32
+// form: the corner with the largest weight adds the parcel's exact volume minus the other
+// seven, so that the corners add up to exactly the parcel's volume. A position outside the
+// box or not finite, or a value out of the fixed-point range, sets a flag (the output is
+// then NaN); such a parcel is clamped into the edge cells for its deposit.
 template <class T>
 __global__ void k_deposit_static(KParams<T> p, const T* __restrict__ x, const T* __restrict__ y,
                                  const T* __restrict__ z, const T* __restrict__ d,
@@ -1279,27 +1380,47 @@ __global__ void k_deposit_static(KParams<T> p, const T* __restrict__ x, const T*
   constexpr int W = Words<T>::n;
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
+  const T pos[3] = {x[q], y[q], z[q]};
+  for (int a = 0; a < 3; ++a)
+    if (!(pos[a] >= T(0) && pos[a] <= p.L[a])) atomicOr(p.errs, ERR_DOMAIN);
   Cell3<T> c;
-  bin3(p, x[q], y[q], z[q], c);
+  bin3(p, pos[0], pos[1], pos[2], c);
   T dq = d[q];
   T V = om[q] * (dq * dq * dq) * p.vcoef;
   T w[3][2];
   for (int a = 0; a < 3; ++a) { w[a][0] = T(1) - c.xi[a]; w[a][1] = c.xi[a]; }
+  const int kst = (c.xi[0] >= T(0.5) ? 1 : 0) + (c.xi[1] >= T(0.5) ? 2 : 0) + (c.xi[2] >= T(0.5) ? 4 : 0);
+  long long rest = 0;
+  if (W == 1) {
+    u64 tot[W];
+    to_fixed(V, p.mV, tot, p.errs);
+    rest = (long long)tot[0];
+  }
   for (int cc = 0; cc < 2; ++cc)
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
+        const int k = a + 2 * b + 4 * cc;
+        if (W == 1 && k == kst) continue;
         u64 fx[W];
         to_fixed(V * ((w[0][a] * w[1][b]) * w[2][cc]), p.mV, fx, p.errs);
+        if (W == 1) rest -= (long long)fx[0];
         acc_add(acc + node_id(p, c.i + a, c.j + b, c.k + cc), p.nnode, fx);  // single bed
       }
+  if (W == 1) {
+    u64 fx[W];
+    fx[0] = (u64)rest;
+    acc_add(acc + node_id(p, c.i + (kst & 1), c.j + ((kst >> 1) & 1), c.k + (kst >> 2)), p.nnode, fx);
+  }
 }
 
+// The accumulator as doubles; every output is NaN if a parcel raised a flag.
 template <class T>
-__global__ void k_static_out(const u64* __restrict__ acc, long long nnode, double inv_m,
-                             double* __restrict__ out) {
+__global__ void k_static_out(const u64* __restrict__ acc, const int* __restrict__ errs,
+                             long long nnode, double inv_m, double* __restrict__ out) {
   constexpr int W = Words<T>::n;
   long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= nnode) return;
+  if (*errs) { out[n] = __longlong_as_double(0x7ff8000000000000ll); return; }
   u64 fx[W];
   for (int w = 0; w < W; ++w) fx[w] = acc[(long long)w * nnode + n];
   out[n] = from_fixed(fx, inv_m);
@@ -1315,15 +1436,15 @@ mppic_status deposit_static_impl(const mppic_config* c, const mppic_parcels* pc,
   p.nnode = (long long)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
   p.nstride = p.nnode;
   const double hs[3] = {c->dx, c->dy, c->dz};
+  const int ns[3] = {c->nx, c->ny, c->nz};
   for (int a = 0; a < 3; ++a) {
     p.inv_d[a] = 1.0 / hs[a];
     p.inv_f[a] = (float)p.inv_d[a];
     p.inv_lo[a] = (float)(p.inv_d[a] - (double)p.inv_f[a]);
+    p.L[a] = (T)(ns[a] * hs[a]);
   }
   p.vcoef = (T)(M_PI / 6.0 * c->dscale * c->dscale * c->dscale);
-  const double vcell = c->dx * c->dy * c->dz;
-  const double mV = std::ldexp(1.0, sizeof(T) == 4 ? 48 : 96) / vcell;
-  p.mV = (T)mV;
+  fixed_units(*c, sizeof(T), &p.mV, &p.mA);
   u64* acc = base + 32;                         // the first 256 bytes hold the flag word
   p.errs = reinterpret_cast<int*>(base);
   CU(cudaMemsetAsync(base, 0, sizeof(u64) * (32 + (size_t)Words<T>::n * p.nnode), st));
@@ -1334,7 +1455,8 @@ mppic_status deposit_static_impl(const mppic_config* c, const mppic_parcels* pc,
         static_cast<const T*>(pc->omega), pc->np, acc);
     LAUNCHED();
   }
-  k_static_out<T><<<blocks(p.nnode, 256), 256, 0, st>>>(acc, p.nnode, 1.0 / (double)p.mV, Vs_out);
+  k_static_out<T><<<blocks(p.nnode, 256), 256, 0, st>>>(acc, p.errs, p.nnode, 1.0 / (double)p.mV,
+                                                       Vs_out);
   LAUNCHED();
   return MPPIC_OK;
 }
@@ -1348,6 +1470,7 @@ extern "C" mppic_status mppic_deposit_static(const mppic_config* cfg, const mppi
     return fail(h, MPPIC_ERR_INVALID, "cfg, parcels and Vs_out must not be NULL");
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || !(cfg->dx > 0 && cfg->dy > 0 && cfg->dz > 0))
     return fail(h, MPPIC_ERR_INVALID, "grid and spacing must be positive");
+  if (!(cfg->dscale > 0)) return fail(h, MPPIC_ERR_INVALID, "dscale must be positive");
   if (cfg->precision != 32 && cfg->precision != 64)
     return fail(h, MPPIC_ERR_INVALID, "precision must be 32 or 64, got %d", cfg->precision);
   const long long nnode = (long long)(cfg->nx + 1) * (cfg->ny + 1) * (cfg->nz + 1);
@@ -1362,13 +1485,23 @@ extern "C" mppic_status mppic_deposit_static(const mppic_config* cfg, const mppi
   int dev = 0;
   CU(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(h, MPPIC_ERR_INVALID, "device %d unsupported", dev);
-  if (!g_static_addr[dev]) {             // set-up, once per device, with the device current
-    void* addr = nullptr;
-    CU(cudaGetSymbolAddress(&addr, g_static_scratch));
-    g_static_addr[dev] = addr;
-  }
-  u64* base = static_cast<u64*>(g_static_addr[dev]);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Outside stream capture the address is looked up on every call (cheap, allocates nothing),
+  // so a device reset or a re-created context cannot leave a stale one; during capture the
+  // last address looked up on this device is used.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(st, &cap));
+  void* addr = nullptr;
+  if (cap == cudaStreamCaptureStatusNone) {
+    CU(cudaGetSymbolAddress(&addr, g_static_scratch));
+    g_static_addr[dev].store(addr);
+  } else {
+    addr = g_static_addr[dev].load();
+    if (!addr)
+      return fail(h, MPPIC_ERR_INVALID,
+                  "mppic_deposit_static: make a first call on this device outside stream capture");
+  }
+  u64* base = static_cast<u64*>(addr);
   return cfg->precision == 32 ? deposit_static_impl<float>(cfg, parcels, Vs_out, st, base)
                               : deposit_static_impl<double>(cfg, parcels, Vs_out, st, base);
 }

@@ -32,6 +32,11 @@ constexpr int TX = BX + 1, TY = BY + 1, TZ = BZ + 1;
 constexpr int TNODES = TX * TY * TZ;             // 405 nodes per brick tile
 constexpr int NQ = 5;                            // Vs, A, Bx, By, Bz
 constexpr int ERR_DOMAIN = 1, ERR_RANGE = 2, ERR_TIMEOUT = 4;
+// drag closures (the drag_model field of the configuration)
+constexpr int DRAG_WEN_YU = 0, DRAG_SYAMLAL_OBRIEN = 1, DRAG_GIDASPOW = 2, DRAG_GIDASPOW_BLEND = 3;
+// cell kernel modes: the solids volume only; a full step; the drag sums only (a gas
+// iteration of implicit coupling)
+constexpr int MODE_VOLUME = 0, MODE_STEP = 1, MODE_DRAG = 2;
 
 typedef unsigned long long u64;
 
@@ -58,7 +63,11 @@ struct KParams {
   T kRe;                     // rho_g / mu_g (Re_m = eps_g d |s| kRe)
   T kD1, kD2;                // C 18 mu / rho_p and C 0.33 rho_g / rho_p (drag prefactors)
   T kD1u, kD2u;              // the same without C
-  T mV, mA;                  // fixed-point multipliers (value * m = integer units)
+  T kE1, kE2;                // Ergun: C 150 mu / rho_p and C 1.75 rho_g / rho_p
+  T kS1, kS2;                // Syamlal-O'Brien: C 3/4 rho_g / rho_p and mu / rho_g
+  int drag_model;            // DRAG_WEN_YU, DRAG_SYAMLAL_OBRIEN, DRAG_GIDASPOW, DRAG_GIDASPOW_BLEND
+  T mV, mA;                  // fixed-point multipliers (value * m = integer units), powers of
+                             // two, so that a value's product with them is exact
   double inv_mV, inv_mA;
   T u_in;
   // node fields: 0 eps_s, 1-3 u_g, 4 tau; 5-7 grad p (caller arrays, used if has_gp)
@@ -96,29 +105,27 @@ __device__ __forceinline__ void bin_axis(double x, double inv_d, float, float, i
   xi = fmin(fmax(xi, 0.0), 1.0);
 }
 
-// FP32 form: the same integer result as the FP64 formula. The FP32 product is within
-// 1.2e-7 |t| of the FP64 one, so away from a face its floor is the same; within
-// 2.5e-7 |t| of a face the FP64 formula decides. The in-cell coordinate is computed
-// with the product's exact rounding error and the low part of 1/h, so it does not lose
-// the digits of i (about 1e-7 absolute instead of |t| * 6e-8).
+// FP32 form: the same integer result as the FP64 formula. r = fma(x, inv_lo, fma(x, inv_f, -i))
+// (inv_f + inv_lo = 1/h to about 2^-48 relative) is the in-cell coordinate x/h - i to within
+// 1.3e-7 absolute, whatever the size of i: the inner fused multiply-add rounds once a value
+// below 2 in magnitude, the outer adds the low part of the product. So where 2.5e-7 <= r <=
+// 1 - 2.5e-7 the FP64 formula's floor is i as well; within 2.5e-7 of a face the FP64 formula
+// decides.
 __device__ __forceinline__ void bin_axis(float x, double inv_d, float inv_f, float inv_lo, int n,
                                          int& i, float& xi) {
-  float t = __fmul_rn(x, inv_f);
-  float fl = floorf(t);
-  float r = __fsub_rn(t, fl);
-  float tol = fabsf(t) * 2.5e-7f;
-  if (!(r >= tol && r <= 1.0f - tol)) {
+  float fl = floorf(__fmul_rn(x, inv_f));
+  float r = __fmaf_rn(x, inv_lo, __fmaf_rn(x, inv_f, -fl));
+  if (!(r >= 2.5e-7f && r <= 1.0f - 2.5e-7f)) {
     double f64 = floor(__dmul_rn((double)x, inv_d));
     if (!(f64 >= 0.0)) f64 = 0.0;
     if (f64 > (double)(n - 1)) f64 = (double)(n - 1);
     fl = (float)f64;
+    r = __fmaf_rn(x, inv_lo, __fmaf_rn(x, inv_f, -fl));
   }
   if (!(fl >= 0.0f)) fl = 0.0f;
   if (fl > (float)(n - 1)) fl = (float)(n - 1);
   i = (int)fl;
-  float lo = __fmaf_rn(x, inv_f, -t);
-  xi = __fadd_rn(__fadd_rn(__fsub_rn(t, fl), lo), __fmul_rn(x, inv_lo));
-  xi = fminf(fmaxf(xi, 0.0f), 1.0f);
+  xi = fminf(fmaxf(r, 0.0f), 1.0f);
 }
 
 template <class T>
@@ -145,12 +152,9 @@ __device__ __forceinline__ bool xi_in_cell(double x, double inv_d, float, float,
   return true;
 }
 __device__ __forceinline__ bool xi_in_cell(float x, double, float inv_f, float inv_lo, int ic, float& xi) {
-  const float t = __fmul_rn(x, inv_f);
-  const float d = __fsub_rn(t, (float)ic);
-  const float tol = fabsf(t) * 2.5e-7f;
-  if (!(d >= tol && d <= 1.0f - tol)) return false;
-  const float lo = __fmaf_rn(x, inv_f, -t);
-  xi = __fadd_rn(__fadd_rn(d, lo), __fmul_rn(x, inv_lo));
+  const float r = __fmaf_rn(x, inv_lo, __fmaf_rn(x, inv_f, -(float)ic));
+  if (!(r >= 2.5e-7f && r <= 1.0f - 2.5e-7f)) return false;
+  xi = r;
   return true;
 }
 
@@ -503,8 +507,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // warp shares the work: in rounds of four such lanes, lanes 8g..8g+7 take the 8 corners of
 // the g-th, instead of each lane running its 8 corners while the rest of the warp idles.
 // Integer additions commute, so neither the order of these calls nor the rounds change any
-// sum.
-template <class T, int NV>
+// sum. EXACT (the solids volume of the FP32 form): the corner with the largest weight adds
+// the parcel's volume in fixed point minus the other seven corners' values, so that the 8
+// corners add up to exactly the parcel's volume (v0 * mV is exact: mV is a power of two).
+template <class T, int NV, bool EXACT = false>
 __device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* fx, int* kr, int i0,
                                                   int j0, int k0, unsigned pend, CellBits cb, int cell, T x0, T x1,
                                                   T x2, int q0, T v0, T v1, T v2, T v3) {
@@ -526,8 +532,21 @@ __device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* f
       vals[2] = __shfl_sync(FULL, v2, s);
       vals[3] = __shfl_sync(FULL, v3, s);
     }
+    const T Wq = ((a ? y0 : T(1) - y0) * (b ? y1 : T(1) - y1)) * (c ? y2 : T(1) - y2);
+    u64 fe[W] = {};
+    if (EXACT) {                                 // all 32 lanes: the group sum of the others
+      const int kst = (y0 >= T(0.5) ? 1 : 0) + (y1 >= T(0.5) ? 2 : 0) + (y2 >= T(0.5) ? 4 : 0);
+      to_fixed(has ? vals[0] * Wq : T(0), p.mV, fe, p.errs);
+      long long others = corner == kst ? 0ll : (long long)fe[0];
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) others += __shfl_xor_sync(FULL, others, o);
+      if (corner == kst) {
+        u64 tot[W];
+        to_fixed(has ? vals[0] : T(0), p.mV, tot, p.errs);
+        fe[0] = (u64)((long long)tot[0] - others);
+      }
+    }
     if (has) {
-      const T Wq = ((a ? y0 : T(1) - y0) * (b ? y1 : T(1) - y1)) * (c ? y2 : T(1) - y2);
       const int ti = si - i0, tj = sj - j0, tk = sk - k0;
       const bool in = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
       if (corner == 0) {                         // node layers deposited into (shared)
@@ -538,7 +557,11 @@ __device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* f
       for (int v = 0; v < NV; ++v) {
         const int qq = q0 + v;
         u64 f[W];
-        to_fixed(vals[v] * Wq, qq == 0 ? p.mV : p.mA, f, p.errs);
+        if (EXACT) {
+          f[0] = fe[0];
+        } else {
+          to_fixed(vals[v] * Wq, qq == 0 ? p.mV : p.mA, f, p.errs);
+        }
         if (in)
           acc_add(fx + (qq * W) * TNODES + (ti + a) + TX * ((tj + b) + TY * (tk + c)), TNODES, f);
         else
@@ -762,6 +785,78 @@ __device__ __forceinline__ double wen_yu_step(const KParams<double>& p, double d
   return wen_yu_fast(p, d, es, s);
 }
 
+// Syamlal-O'Brien drag (the paper's closure, Sec. 2.1) as an acceleration coefficient:
+// D = C 3/4 C_D eps_g rho_g |s| / (V_r^2 d rho_p) with Dallavalle's C_D at Re / V_r and the
+// velocity ratio V_r of Re = rho_g d |s| / mu, A = eps_g^4.14 and B = 0.8 eps_g^1.28
+// (eps_g <= 0.85) or eps_g^2.65, evaluated as
+//   V_r = (A + t / (sqrt(r^2 + t) + r)) / 2,  r = 0.06 Re,  t = A^2 + 2r (2B - A)
+// (no cancellation: t > 0 since A < 2B) and C_D |s| = (0.63 sqrt|s| + 4.8 sqrt(V_r mu /
+// (rho_g d)))^2, finite at zero slip.
+__device__ __forceinline__ float syamlal_obrien_step(const KParams<float>& p, float d, float es,
+                                                     const float (&s)[3]) {
+  const float eg = fmaxf(1.0f - es, p.eg_min);
+  const float de = p.sd * d;
+  const float inv_de = __fdividef(1.0f, de);
+  const float s2 = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
+  const float smag = s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f;
+  const float r = 0.06f * (p.kRe * de * smag);
+  const float lg = __log2f(eg);
+  const float A = exp2f(4.14f * lg);
+  const float B = eg <= 0.85f ? 0.8f * exp2f(1.28f * lg) : exp2f(2.65f * lg);
+  const float t = A * A + 2.0f * r * (2.0f * B - A);
+  const float vr = 0.5f * (A + __fdividef(t, sqrtf(r * r + t) + r));
+  const float root = 0.63f * sqrtf(smag) + 4.8f * sqrtf(vr * p.kS2 * inv_de);
+  return p.kS1 * root * root * eg * __fdividef(inv_de, vr * vr);
+}
+__device__ __forceinline__ double syamlal_obrien_step(const KParams<double>& p, double d, double es,
+                                                      const double (&s)[3]) {
+  const double eg = fmax(1.0 - es, p.eg_min);
+  const double de = p.sd * d;
+  const double smag = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+  const double r = 0.06 * (p.kRe * de * smag);
+  const double A = pow(eg, 4.14);
+  const double B = eg <= 0.85 ? 0.8 * pow(eg, 1.28) : pow(eg, 2.65);
+  const double t = A * A + 2.0 * r * (2.0 * B - A);
+  const double vr = 0.5 * (A + t / (sqrt(r * r + t) + r));
+  const double root = 0.63 * sqrt(smag) + 4.8 * sqrt(vr * p.kS2 / de);
+  return p.kS1 * root * root * eg / (vr * vr * de);
+}
+
+// Ergun's dense-bed drag as an acceleration coefficient: D = C (150 eps_s mu / (eps_g d^2) +
+// 1.75 rho_g |s| / d) / rho_p, with eps_s = 1 - eps_g of the floored voidage.
+template <class T>
+__device__ __forceinline__ T ergun_step(const KParams<T>& p, T d, T es, const T (&s)[3]) {
+  const T eg = tmax(T(1) - es, p.eg_min);
+  const T inv_de = frcp(p.sd * d);
+  const T smag = fsqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+  return p.kE1 * (T(1) - eg) * frcp(eg) * (inv_de * inv_de) + p.kE2 * smag * inv_de;
+}
+
+// Gidaspow drag: Ergun below a voidage of 0.8, Wen-Yu at and above it; the blend weights them
+// with phi = atan(262.5 (0.2 - eps_s)) / pi + 1/2 (Wen-Yu weight), eps_s = 1 - floored eps_g.
+__device__ __forceinline__ float tatan(float a) { return atanf(a); }
+__device__ __forceinline__ double tatan(double a) { return atan(a); }
+template <class T>
+__device__ __forceinline__ T gidaspow_step(const KParams<T>& p, T d, T es, const T (&s)[3], bool blend) {
+  const T eg = tmax(T(1) - es, p.eg_min);
+  if (!blend) return eg < T(0.8) ? ergun_step(p, d, es, s) : wen_yu_step(p, d, es, s);
+  const T phi = tatan(T(262.5) * (T(0.2) - (T(1) - eg))) * T(0.31830988618379067) + T(0.5);
+  return (T(1) - phi) * ergun_step(p, d, es, s) + phi * wen_yu_step(p, d, es, s);
+}
+
+// The drag closure of the step kernels. DRAG = 0: Wen-Yu only (the fast path); DRAG = 1: the
+// closure each bed's drag_model names.
+template <class T, int DRAG>
+__device__ __forceinline__ T drag_step(const KParams<T>& p, T d, T es, const T (&s)[3]) {
+  if (DRAG == 0) return wen_yu_step(p, d, es, s);
+  switch (p.drag_model) {
+    case DRAG_SYAMLAL_OBRIEN: return syamlal_obrien_step(p, d, es, s);
+    case DRAG_GIDASPOW: return gidaspow_step(p, d, es, s, false);
+    case DRAG_GIDASPOW_BLEND: return gidaspow_step(p, d, es, s, true);
+    default: return wen_yu_step(p, d, es, s);
+  }
+}
+
 // Deterministic sum of three per-thread values over the CTA: a fixed shuffle tree in
 // each warp, then the warp partials in warp order.
 template <class T>
@@ -787,32 +882,42 @@ __device__ void cta_sum3(T a, T b, T c, T* sm, double* out) {
 // warp w the group of threads 32w..32w+31, whose parcels are stored by level
 // (level_layout, at each sort). The warp's r-th iteration processes the r-th parcel of
 // each of its cells that has one, one per thread, with coalesced loads and stores.
-// MODE 0: deposit the solids volume of the current positions.
-// MODE 1: one full step (interp from a shared node-field tile, drag, drag sums,
+// MODE_VOLUME: deposit the solids volume of the current positions.
+// MODE_STEP: one full step (interp from a shared node-field tile, drag, drag sums,
 // objectives, push, walls, re-bin), depositing the solids volume of the new positions
 // for the next step. src/dst may be the same arrays; if not, the read-only arrays are
 // copied too. key_out (nullable) receives the sort key of every new position (the step
 // before a sort, so the sort needs no key pass).
+// MODE_DRAG: the drag sums A, B of the current state against the current node gas velocity,
+// parcels unchanged (a gas iteration of implicit coupling).
 // A thread sums the contributions of its own cell's parcels (old position for the drag
-// sums, new position for the volume) at the cell's 8 corners in registers: 40 sums, added
-// once per brick to a shared node tile in 8 corner phases (no two cells of a phase share a
-// node). A parcel that is not in its sorted cell (it drifted since the last sort, or
-// moved this step) adds its contributions in exact fixed point to a second shared tile
-// (or, outside the brick, to the global accumulators). Both tiles go to the global
-// accumulators in fixed point once per brick. Threads wait on each other only at the
-// brick's start and end.
+// sums, new position for the volume) at the cell's 8 corners in registers: up to 40 sums,
+// added once per brick to a shared node tile in 8 corner phases (no two cells of a phase
+// share a node). In the FP32 form the thread also sums its parcels' volumes exactly in
+// fixed point, and the corner with the largest sum takes that total minus the other seven,
+// so the deposited volume of a cell is exactly the sum of its parcels' volumes. A parcel
+// that is not in its sorted cell (it drifted since the last sort, or moved this step) adds
+// its contributions in exact fixed point to a second shared tile (or, outside the brick,
+// to the global accumulators). Both tiles go to the brick's slot in fixed point once per
+// brick. Threads wait on each other only at the brick's start and end.
+// DRAG: 0 Wen-Yu only, 1 the drag closure of each bed's drag_model.
 template <class T> struct CellOccupancy;
 template <> struct CellOccupancy<float> { static constexpr int ctas = 2; };
 template <> struct CellOccupancy<double> { static constexpr int ctas = 1; };
 
-template <class T, int MODE>
+// BATCH: the parameters of each brick's bed come from `beds` (copied to shared memory when
+// the bed changes); otherwise from p0, which the kernel reads in place from its constant
+// parameter space (no copy, no per-use shared-memory load).
+template <class T, int MODE, int DRAG, bool BATCH>
 __global__ void __launch_bounds__(BCELLS, CellOccupancy<T>::ctas)
-k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restrict__ brick_bed,
-        long long total_bricks, unsigned long long* __restrict__ work, PArrays<T> src,
-        PArrays<T> dst, int* __restrict__ cell_out, uint32_t* __restrict__ key_out,
-        double* __restrict__ obj_part, long long np) {
+k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ beds,
+        const int* __restrict__ brick_bed, long long total_bricks,
+        unsigned long long* __restrict__ work, PArrays<T> src, PArrays<T> dst,
+        int* __restrict__ cell_out, uint32_t* __restrict__ key_out, double* __restrict__ obj_part,
+        long long np) {
   typedef CellSmem<T> S;
   constexpr int W = S::W;
+  constexpr bool EXACT_V = W == 1 && MODE != MODE_DRAG;  // FP32 form: exact cell volume totals
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ KParams<T> sp;                        // parameters of the current brick's bed
   __shared__ long long s_brick;
@@ -827,24 +932,15 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const unsigned below = (1u << lane) - 1u;
-  const KParams<T>& p = sp;
   int cur_bed = -1;
   const bool copy_ro = src.a[0] != dst.a[0];
-  const int nq = MODE == 1 ? NQ : 1;
-  const int epoch = *(beds ? beds[0].epoch : p0.epoch);
+  // quantities this mode deposits: [q0, q1)
+  constexpr int q0 = MODE == MODE_DRAG ? 1 : 0;
+  constexpr int q1 = MODE == MODE_VOLUME ? 1 : NQ;
+  const int epoch = *(BATCH ? beds[0].epoch : p0.epoch);
 
-  for (long long iter = 0; iter < total_bricks; ++iter) {
-  __syncthreads();
-  if (tid == 0) s_brick = (long long)atomicAdd(work, 1ull);
-  __syncthreads();
-  const long long b = s_brick;
-  if (b >= total_bricks) break;
-  const int bed = beds ? brick_bed[b] : 0;
-  if (bed != cur_bed) {
-    if (tid == 0) sp = beds ? beds[bed] : p0;
-    cur_bed = bed;
-    __syncthreads();
-  }
+  // one brick, with its bed's parameters p
+  auto brick = [&](const KParams<T>& p, const long long b) {
   const unsigned bu = (unsigned)(b - p.bbase);   // brick within its bed
   const int bi0 = (int)(bu % (unsigned)p.nbx) * BX;
   const int bj0 = (int)((bu / (unsigned)p.nbx) % (unsigned)p.nby) * BY;
@@ -852,8 +948,8 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   const CellBits cb = cell_bits(p);
   const long long kbase = b * BCELLS;
   if (p.cstart[kbase] == p.cstart[kbase + BCELLS]) {
-    if (MODE == 1 && tid == 0) { obj_part[3 * b] = 0; obj_part[3 * b + 1] = 0; obj_part[3 * b + 2] = 0; }
-    continue;
+    if (MODE == MODE_STEP && tid == 0) { obj_part[3 * b] = 0; obj_part[3 * b + 1] = 0; obj_part[3 * b + 2] = 0; }
+    return;
   }
 
   // this thread's cell (from the cell map of the last sort) and its parcels
@@ -865,17 +961,19 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     const int ws = __reduce_add_sync(FULL, n);
     if (lane == 0) s_wsum[warp] = ws;
   }
-  for (int e = tid; e < nq * W * TNODES; e += BCELLS) fx[e] = 0;
-  for (int e = tid; e < nq * TNODES; e += BCELLS) tile[e] = 0;
+  for (int e = tid + q0 * W * TNODES; e < q1 * W * TNODES; e += BCELLS) fx[e] = 0;
+  for (int e = tid + q0 * TNODES; e < q1 * TNODES; e += BCELLS) tile[e] = 0;
   if (tid == 0) { s_kr[0] = 1 << 30; s_kr[1] = -1; }
-  if (MODE == 1) {
-    // asynchronous copies, all in flight at once; absent nodes and fields are zero
+  if (MODE != MODE_VOLUME) {
+    // asynchronous copies, all in flight at once; absent nodes and fields are zero. The drag
+    // sums need only eps_s and u_g.
+    constexpr int nf = MODE == MODE_DRAG ? 4 : 8;
     for (int tn = tid; tn < TNODES; tn += BCELLS) {
       const int i = bi0 + tn % TX, j = bj0 + (tn / TX) % TY, k = bk0 + tn / (TX * TY);
       const bool in = i <= p.nx && j <= p.ny && k <= p.nz;
       const long long nid = in ? node_id(p, i, j, k) : 0;
 #pragma unroll
-      for (int f = 0; f < 8; ++f) {
+      for (int f = 0; f < nf; ++f) {
         if (f >= 5 && !p.has_gp) continue;       // grad p planes are read only for a node field
         T* dstv = sf + tile_off<T>(f, tn);
         if (in)
@@ -895,6 +993,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   for (int w = 0; w < warp; ++w) off += s_wsum[w];
   CellSums<T> sums;
   sums.zero();
+  long long vtot = 0;                            // EXACT_V: this cell's volume, fixed point
   T o_dp = 0, o_hn = 0, o_vs = 0;
 
   // Level r's parcel values are copied into this thread's slots of stage r % PSTAGES
@@ -909,7 +1008,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
       T* slot = pre + (lv % PSTAGES) * 8 * BCELLS + tid;
 #pragma unroll
       for (int f = 0; f < 8; ++f)
-        if (MODE == 1 || f < 3 || f >= 6) cp_async(slot + f * BCELLS, src.a[f] + q);
+        if (MODE != MODE_VOLUME || f < 3 || f >= 6) cp_async(slot + f * BCELLS, src.a[f] + q);
     }
     pf_off += __popc(bl);
   };
@@ -941,12 +1040,13 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         co = pack_cell(p, cb, c.i, c.j, c.k);
         xo[0] = c.xi[0]; xo[1] = c.xi[1]; xo[2] = c.xi[2];
       }
-      if (MODE == 0) {
+      if (MODE == MODE_VOLUME) {
         if (own) {
           W8<T> Wq;
           T yz[4];
           corner_weights(c.xi, Wq, yz);
           sums.add_vol(V, Wq);
+          if (EXACT_V) { u64 vf[W]; to_fixed(V, p.mV, vf, p.errs); vtot += (long long)vf[0]; }
         } else {
           off_old = true;
         }
@@ -968,11 +1068,8 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
         }
         T up[3] = {u, v, w};
         const T s[3] = {I.ug[0] - u, I.ug[1] - v, I.ug[2] - w};
-        const T D = wen_yu_step(p, d, I.es, s);
+        const T D = drag_step<T, DRAG>(p, d, I.es, s);
         const T f = p.rho_p * V * D;
-        o_dp += f * s[2];
-        o_hn += V * z;
-        o_vs += V;
         // drag sums of the pre-push state, at the old position
         if (own) {
           sums.add_drag(f, f * u, f * v, f * w, wt.W);
@@ -980,60 +1077,67 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
           off_old = true;
           fd[0] = f; fd[1] = f * u; fd[2] = f * v; fd[3] = f * w;
         }
-        // semi-implicit push (Eq. 4 / (eps_P rho_P), drag implicit), Eq. 3, specular walls
-        T pos[3] = {x, y, z};
-        const T inv_den = frcp(T(1) + p.dt * D);
-        const T inv_esr = I.es > T(1e-12) ? frcp(I.es * p.rho_p) : T(0);
-        bool bad = false;
+        if (MODE == MODE_STEP) {
+          o_dp += f * s[2];
+          o_hn += V * z;
+          o_vs += V;
+          // semi-implicit push (Eq. 4 / (eps_P rho_P), drag implicit), Eq. 3, specular walls
+          T pos[3] = {x, y, z};
+          const T inv_den = frcp(T(1) + p.dt * D);
+          const T inv_esr = I.es > T(1e-12) ? frcp(I.es * p.rho_p) : T(0);
+          bool bad = false;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const T acc = D * I.ug[a] + p.g[a] - I.gp[a] * p.inv_rho_p - I.gt[a] * inv_esr;
-          T un = (up[a] + p.dt * acc) * inv_den;
-          T xn = pos[a] + p.dt * un;
-          if (xn < T(0)) { xn = -xn; un = -p.e_wall * un; }
-          else if (xn > p.L[a]) { xn = T(2) * p.L[a] - xn; un = -p.e_wall * un; }
-          if (!(xn >= T(0) && xn <= p.L[a]) || !isfinite(un)) bad = true;
-          pos[a] = xn;
-          up[a] = un;
+          for (int a = 0; a < 3; ++a) {
+            const T acc = D * I.ug[a] + p.g[a] - I.gp[a] * p.inv_rho_p - I.gt[a] * inv_esr;
+            T un = (up[a] + p.dt * acc) * inv_den;
+            T xn = pos[a] + p.dt * un;
+            if (xn < T(0)) { xn = -xn; un = -p.e_wall * un; }
+            else if (xn > p.L[a]) { xn = T(2) * p.L[a] - xn; un = -p.e_wall * un; }
+            // a non-finite velocity makes the position non-finite, which fails this test too
+            if (!(xn >= T(0) && xn <= p.L[a])) bad = true;
+            pos[a] = xn;
+            up[a] = un;
+          }
+          if (bad) atomicOr(p.errs, ERR_DOMAIN);
+          // solids volume of the new position, for the next step
+          Cell3<T> cn;
+          if (bin3_expect(p, pos[0], pos[1], pos[2], ci, cj, ck, cn)) {
+            W8<T> Wq;
+            T yz[4];
+            corner_weights(cn.xi, Wq, yz);
+            sums.add_vol(V, Wq);
+            if (EXACT_V) { u64 vf[W]; to_fixed(V, p.mV, vf, p.errs); vtot += (long long)vf[0]; }
+          } else {
+            off_new = true;
+            cno = pack_cell(p, cb, cn.i, cn.j, cn.k);
+            xno[0] = cn.xi[0]; xno[1] = cn.xi[1]; xno[2] = cn.xi[2];
+          }
+          dst.a[0][q] = pos[0]; dst.a[1][q] = pos[1]; dst.a[2][q] = pos[2];
+          dst.a[3][q] = up[0]; dst.a[4][q] = up[1]; dst.a[5][q] = up[2];
+          if (copy_ro) {
+            dst.a[6][q] = d; dst.a[7][q] = om;
+            if (src.pid) dst.pid[q] = src.pid[q];
+            if (src.tag) dst.tag[q] = src.tag[q];
+          }
+          if (cell_out) cell_out[q] = cell_id(p, cn.i, cn.j, cn.k);
+          if (key_out) key_out[q] = (uint32_t)(p.bbase * BCELLS) + brick_key(p, cn.i, cn.j, cn.k);
         }
-        if (bad) atomicOr(p.errs, ERR_DOMAIN);
-        // solids volume of the new position, for the next step
-        Cell3<T> cn;
-        if (bin3_expect(p, pos[0], pos[1], pos[2], ci, cj, ck, cn)) {
-          W8<T> Wq;
-          T yz[4];
-          corner_weights(cn.xi, Wq, yz);
-          sums.add_vol(V, Wq);
-        } else {
-          off_new = true;
-          cno = pack_cell(p, cb, cn.i, cn.j, cn.k);
-          xno[0] = cn.xi[0]; xno[1] = cn.xi[1]; xno[2] = cn.xi[2];
-        }
-        dst.a[0][q] = pos[0]; dst.a[1][q] = pos[1]; dst.a[2][q] = pos[2];
-        dst.a[3][q] = up[0]; dst.a[4][q] = up[1]; dst.a[5][q] = up[2];
-        if (copy_ro) {
-          dst.a[6][q] = d; dst.a[7][q] = om;
-          if (src.pid) dst.pid[q] = src.pid[q];
-          if (src.tag) dst.tag[q] = src.tag[q];
-        }
-        if (cell_out) cell_out[q] = cell_id(p, cn.i, cn.j, cn.k);
-        if (key_out) key_out[q] = (uint32_t)(p.bbase * BCELLS) + brick_key(p, cn.i, cn.j, cn.k);
       }
     }
     {
       const unsigned po = __ballot_sync(FULL, off_old);
       if (po) {
-        if (MODE == 0)
-          deposit_foreign_warp<T, 1>(p, fx, s_kr, bi0, bj0, bk0, po, cb, co, xo[0], xo[1], xo[2], 0, V,
-                                     T(0), T(0), T(0));
+        if (MODE == MODE_VOLUME)
+          deposit_foreign_warp<T, 1, EXACT_V>(p, fx, s_kr, bi0, bj0, bk0, po, cb, co, xo[0], xo[1], xo[2],
+                                              0, V, T(0), T(0), T(0));
         else
           deposit_foreign_warp<T, 4>(p, fx, s_kr, bi0, bj0, bk0, po, cb, co, xo[0], xo[1], xo[2], 1, fd[0],
                                      fd[1], fd[2], fd[3]);
       }
-      const unsigned pn = MODE == 1 ? __ballot_sync(FULL, off_new) : 0u;
+      const unsigned pn = MODE == MODE_STEP ? __ballot_sync(FULL, off_new) : 0u;
       if (pn)
-        deposit_foreign_warp<T, 1>(p, fx, s_kr, bi0, bj0, bk0, pn, cb, cno, xno[0], xno[1], xno[2], 0, V,
-                                   T(0), T(0), T(0));
+        deposit_foreign_warp<T, 1, EXACT_V>(p, fx, s_kr, bi0, bj0, bk0, pn, cb, cno, xno[0], xno[1], xno[2],
+                                            0, V, T(0), T(0), T(0));
     }
     off += __popc(bal);
   }
@@ -1044,15 +1148,36 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     const int khi = __reduce_max_sync(FULL, n > 0 ? ck + 1 : -1);
     if (lane == 0 && khi >= 0) { atomicMin(&s_kr[0], klo); atomicMax(&s_kr[1], khi); }
   }
-  // ---- this cell's sums into the tile, one corner per phase: in a phase no two cells touch
-  // the same node, so plain adds in a fixed order are deterministic
+  // ---- FP32 volume: the 8 corner sums in fixed point, the largest replaced by the cell's
+  // exact total minus the other seven
+  long long vfx[8];
+  if (EXACT_V) {
+    long long sum7 = 0;
+    int kmax = 0;
+    T vmax = sums.get(0, 0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      u64 f[W];
+      to_fixed(sums.get(0, k), p.mV, f, p.errs);
+      vfx[k] = (long long)f[0];
+      sum7 += vfx[k];
+      if (sums.get(0, k) > vmax) { vmax = sums.get(0, k); kmax = k; }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k == kmax) vfx[k] += vtot - sum7;
+  }
+  // ---- this cell's sums into the tiles, one corner per phase: in a phase no two cells touch
+  // the same node, so plain adds in a fixed order are deterministic (the off-cell atomics
+  // into fx are complete: the loop is over)
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     __syncthreads();
     if (n > 0) {
       const int tn = tn0 + (k & 1) + TX * (((k >> 1) & 1) + TY * (k >> 2));
-      tile[tn] += sums.get(0, k);
-      if (MODE == 1) {
+      if (EXACT_V) fx[tn] += (u64)vfx[k];
+      else if (MODE != MODE_DRAG) tile[tn] += sums.get(0, k);
+      if (MODE != MODE_VOLUME) {
 #pragma unroll
         for (int q = 1; q < NQ; ++q) tile[q * TNODES + tn] += sums.get(q, k);
       }
@@ -1065,7 +1190,7 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
   // node), stamped with this deposit's epoch
   {
     u64* slot = p.bacc + b * (long long)(NQ * W * TNODES);
-    for (int e = tid; e < nq * TNODES; e += BCELLS) {
+    for (int e = tid + q0 * TNODES; e < q1 * TNODES; e += BCELLS) {
       const int qq = e / TNODES, tn = e % TNODES;
       u64 f[W];
       to_fixed(tile[e], qq == 0 ? p.mV : p.mA, f, p.errs);
@@ -1082,7 +1207,26 @@ k_cells(KParams<T> p0, const KParams<T>* __restrict__ beds, const int* __restric
     }
     if (tid == 0) p.bstamp[b] = epoch;
   }
-  if (MODE == 1) cta_sum3(o_dp, o_hn, o_vs, red, obj_part + 3 * b);
+  if (MODE == MODE_STEP) cta_sum3(o_dp, o_hn, o_vs, red, obj_part + 3 * b);
+  };  // one brick
+
+  for (long long iter = 0; iter < total_bricks; ++iter) {
+    __syncthreads();
+    if (tid == 0) s_brick = (long long)atomicAdd(work, 1ull);
+    __syncthreads();
+    const long long b = s_brick;
+    if (b >= total_bricks) break;
+    if (BATCH) {
+      const int bed = brick_bed[b];
+      if (bed != cur_bed) {
+        if (tid == 0) sp = beds[bed];
+        cur_bed = bed;
+        __syncthreads();
+      }
+      brick(sp, b);
+    } else {
+      brick(p0, b);
+    }
   }  // persistent loop
 }
 
@@ -1151,9 +1295,10 @@ __global__ void k_range_roll(int* zr, int* epoch) {
 
 __global__ void k_epoch_next(int* epoch) { *epoch += 1; }
 
-// After the last step of a call: the drag sums A, B of the bricks' tile slots are added to
-// the global accumulators (which then hold the step's complete sums, read by the drag-sum
-// output until the next node pass clears them). Layers of the last deposit only.
+// After the last step of a call: the solids volume of the new positions and the drag sums
+// A, B of the bricks' tile slots are added to the global accumulators (which then hold the
+// step's complete sums, read by the volume and drag-sum outputs until the next call's deposit
+// and node pass clear them). Layers of the last deposit only.
 template <class T>
 __global__ void k_drag_fold(KParams<T> p) {
   constexpr int W = Words<T>::n;
@@ -1165,13 +1310,25 @@ __global__ void k_drag_fold(KParams<T> p) {
   for (int n = klo * layer + blockIdx.x * blockDim.x + threadIdx.x; n < (khi + 1) * layer;
        n += gridDim.x * blockDim.x) {
     const int i = n % nx1, j = (n / nx1) % ny1, k = n / layer;
-    for (int q = 1; q < NQ; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       u64 f[W];
       node_sum(p, ep, q, n, i, j, k, f);
 #pragma unroll
       for (int w = 0; w < W; ++w) p.acc[(long long)(q * W + w) * p.nstride + p.nbase + n] = f[w];
     }
   }
+}
+
+// The solids volume of the last step's new positions as doubles (after k_drag_fold).
+template <class T>
+__global__ void k_vol_out(KParams<T> p, double* __restrict__ Vs) {
+  constexpr int W = Words<T>::n;
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.nnode) return;
+  u64 fx[W];
+  for (int w = 0; w < W; ++w) fx[w] = p.acc[(long long)w * p.nstride + n];
+  if (W == 1 && (long long)fx[0] >= (1ll << 62)) atomicOr(p.errs, ERR_RANGE);
+  Vs[n] = from_fixed(fx, p.inv_mV);
 }
 
 template <class T>
@@ -1200,6 +1357,52 @@ __device__ __forceinline__ void finalize_node(const KParams<T>& p, int ep, int n
   p.fld[3][n] = U2 / egc;
   T den = tmax(p.eps_cp - es, p.alpha * (T(1) - es));
   p.fld[4][n] = p.Ps * tpow(es, p.beta) / den;
+}
+
+// Implicit coupling, one gas iteration at node (i, j, k) (Sec. 2.2.2, with the gas side
+// reduced to the unsteady and interphase terms of Eq. 2, drag implicit): from the drag sums
+// of the last drag deposit,
+//   u_g' = (m u_g0 + B) / (m + A),   m = rho_g eps_g V_n / dt,
+// eps_g the floored voidage of the node and u_g0 = U / eps_g the gas velocity of the step's
+// start. Reads and clears the drag-sum accumulators; writes the node gas velocity. A node
+// whose four drag sums are all zero (no parcel exchanges momentum there) keeps u_g0 as it is.
+template <class T>
+__device__ __forceinline__ void gas_update_node(const KParams<T>& p, int ep, int n, int i, int j,
+                                                int k) {
+  constexpr int W = Words<T>::n;
+  double s[4];
+  for (int q = 1; q < NQ; ++q) {
+    u64 f[W];
+    node_sum(p, ep, q, n, i, j, k, f);
+    if (W == 1 && ((long long)f[0] >= (1ll << 62) || (long long)f[0] <= -(1ll << 62)))
+      atomicOr(p.errs, ERR_RANGE);
+    s[q - 1] = from_fixed(f, p.inv_mA);
+    for (int w = 0; w < W; ++w) p.acc[(long long)(q * W + w) * p.nstride + p.nbase + n] = 0;
+  }
+  if (s[0] == 0.0 && s[1] == 0.0 && s[2] == 0.0 && s[3] == 0.0) return;
+  double vn = p.vcell;
+  if (i == 0 || i == p.nx) vn *= 0.5;
+  if (j == 0 || j == p.ny) vn *= 0.5;
+  if (k == 0 || k == p.nz) vn *= 0.5;
+  const double egc = fmax(1.0 - (double)p.fld[0][n], (double)p.eg_min);
+  const double m = (double)p.rho_g * egc * vn / (double)p.dt;
+  for (int a = 0; a < 3; ++a) {
+    double U = p.U[a] ? (double)p.U[a][n] : 0.0;
+    if (a == 2) U += (double)p.u_in;
+    p.fld[1 + a][n] = (T)((m * (U / egc) + s[1 + a]) / (m + s[0]));
+  }
+}
+
+template <class T>
+__global__ void k_gas_update(KParams<T> p) {
+  const int nx1 = p.nx + 1, ny1 = p.ny + 1;
+  const int layer = nx1 * ny1;
+  const int klo = max(0, min(p.zr[0], p.zr[2])), khi = min(p.nz, max(p.zr[1], p.zr[3]));
+  if (khi < klo) return;
+  const int ep = *p.epoch;
+  for (int n = klo * layer + blockIdx.x * blockDim.x + threadIdx.x; n < (khi + 1) * layer;
+       n += gridDim.x * blockDim.x)
+    gas_update_node(p, ep, n, n % nx1, (n / nx1) % ny1, n / layer);
 }
 
 // Drag sums of the last step as doubles.
@@ -1356,12 +1559,27 @@ __global__ void k_drag_fold_b(const KParams<T>* __restrict__ beds, const long lo
     const int n = (int)(g - noff[bed]);
     const int nx1 = p.nx + 1, ny1 = p.ny + 1;
     const int i = n % nx1, j = (n / nx1) % ny1, k = n / (nx1 * ny1);
-    for (int q = 1; q < NQ; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       u64 f[W];
       node_sum(p, ep, q, n, i, j, k, f);
 #pragma unroll
       for (int w = 0; w < W; ++w) p.acc[(long long)(q * W + w) * p.nstride + p.nbase + n] = f[w];
     }
+  }
+}
+
+// k_gas_update for a batch: every node of every bed.
+template <class T>
+__global__ void k_gas_update_b(const KParams<T>* __restrict__ beds, const long long* __restrict__ noff,
+                               int nbeds, long long total) {
+  const int ep = *beds[0].epoch;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int bed = find_bed(noff, nbeds, g);
+    const KParams<T>& p = beds[bed];
+    const int n = (int)(g - noff[bed]);
+    const int nx1 = p.nx + 1, ny1 = p.ny + 1;
+    gas_update_node(p, ep, n, n % nx1, (n / nx1) % ny1, n / (nx1 * ny1));
   }
 }
 

@@ -39,7 +39,11 @@ class Config(ctypes.Structure):
                 ("eps_g_min", ctypes.c_double), ("e_wall", ctypes.c_double),
                 ("drag_mult", ctypes.c_double), ("dscale", ctypes.c_double),
                 ("u_in", ctypes.c_double), ("dt", ctypes.c_double),
-                ("sort_every", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("sort_every", ctypes.c_int), ("drag_model", ctypes.c_int),
+                ("coupling_iters", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+# drag closures (mppic_config.drag_model)
+DRAG_MODELS = {"wen_yu": 0, "syamlal_obrien": 1, "gidaspow": 2, "gidaspow_blend": 3}
 
 
 class Parcels(ctypes.Structure):
@@ -48,12 +52,12 @@ class Parcels(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_longlong * 6),
+    _fields_ = [("ms", ctypes.c_double * 7), ("launches", ctypes.c_longlong * 7),
                 ("total_launches", ctypes.c_longlong), ("active_bricks", ctypes.c_longlong),
                 ("parcels", ctypes.c_longlong)]
 
 
-PHASES = ("sort", "deposit", "finalize", "step", "reduce", "other")
+PHASES = ("sort", "deposit", "finalize", "step", "reduce", "other", "couple")
 
 
 class Gas(ctypes.Structure):
@@ -93,6 +97,8 @@ def load():
         L.mppic_step.restype = st
         L.mppic_drag_sums.argtypes = [H] + [ctypes.c_void_p] * 4
         L.mppic_drag_sums.restype = st
+        L.mppic_step_volume.argtypes = [H, ctypes.c_void_p]
+        L.mppic_step_volume.restype = st
         L.mppic_check.argtypes = [H]
         L.mppic_check.restype = st
         L.mppic_set_params.argtypes = [H, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -124,6 +130,9 @@ def make_config(params: dict, precision: int = 32, sort_every: int = 10) -> Conf
     c = Config()
     for name, _ in Config._fields_:
         if name in ("precision", "sort_every", "reserved"):
+            continue
+        if name in ("drag_model", "coupling_iters"):
+            setattr(c, name, int(params.get(name, 0)))
             continue
         v = params[name]
         if name in ("g", "gradp"):
@@ -261,6 +270,12 @@ class Bed:
         self._ok(self.L.mppic_drag_sums(self.h, _ptr(A), _ptr(B[0]), _ptr(B[1]), _ptr(B[2])))
         return A, B
 
+    def step_volume(self, device="cuda"):
+        """Solids volume (double, nnode) the last step deposited for the final positions."""
+        Vs = torch.empty(self.nnode, dtype=torch.float64, device=device)
+        self._ok(self.L.mppic_step_volume(self.h, _ptr(Vs)))
+        return Vs
+
     def tune(self, grid_per_sm: int, sort_every: int = -1):
         """Persistent CTAs per SM of the step and deposit kernels (0 = all that fit) and,
         if >= 0, a new sort period."""
@@ -300,8 +315,8 @@ class Bed:
     def profile_read(self) -> dict:
         pr = Profile()
         self._ok(self.L.mppic_profile_read(self.h, ctypes.byref(pr)))
-        return {"ms": {PHASES[i]: pr.ms[i] for i in range(6)},
-                "launches": {PHASES[i]: int(pr.launches[i]) for i in range(6)},
+        return {"ms": {PHASES[i]: pr.ms[i] for i in range(len(PHASES))},
+                "launches": {PHASES[i]: int(pr.launches[i]) for i in range(len(PHASES))},
                 "total_launches": int(pr.total_launches),
                 "active_bricks": int(pr.active_bricks), "parcels": int(pr.parcels)}
 

@@ -164,6 +164,71 @@ def dense_bed(n=32_000_000, nx=128, ny=128, nz=512, seed=SEED_BASE + 3, eps_s=0.
     return Bed(p, parcels, nsteps=nsteps, meta=dict(workload=f"dense_{nx}x{ny}x{nz}"))
 
 
+def _lattice_fill(rng, n, p, kz, sub, jitter):
+    """n parcel positions, one per randomly chosen sub-cell of a sub[0] x sub[1] x sub[2] split
+    of every cell in the bottom kz layers, at the sub-cell centre jittered by up to +-jitter
+    of its size (a jittered lattice, as MP-PIC beds are usually seeded)."""
+    nx, ny = p["nx"], p["ny"]
+    nsub = nx * sub[0] * ny * sub[1] * kz * sub[2]
+    if n > nsub:
+        raise ValueError(f"{n} parcels do not fit {nsub} sub-cells")
+    pick = rng.choice(nsub, size=n, replace=False)
+    hx, hy, hz = p["dx"] / sub[0], p["dy"] / sub[1], p["dz"] / sub[2]
+    ix = pick % (nx * sub[0])
+    r = pick // (nx * sub[0])
+    iy = r % (ny * sub[1])
+    iz = r // (ny * sub[1])
+    x = (ix + 0.5 + jitter * rng.uniform(-1.0, 1.0, n)) * hx
+    y = (iy + 0.5 + jitter * rng.uniform(-1.0, 1.0, n)) * hy
+    z = (iz + 0.5 + jitter * rng.uniform(-1.0, 1.0, n)) * hz
+    return x, y, z
+
+
+def paper_verification_bed(n=2_983_447, seed=SEED_BASE + 6, u_in=0.5, nsteps=500) -> Bed:
+    """The shape of the paper's verification bed (Sec. 3): a 12 x 72 x 12 cm box of 27 x 162 x
+    27 cells (4.44 mm), gas of 1.093 kg/m3 and 1.9e-5 Pa s, 400 um particles of 2000 kg/m3,
+    statistical weight 10, an initial bed 12 cm tall at a gas fraction of 0.42 (2,983,447
+    parcels, the paper's count), inlet velocity in the paper's 0.3-1.0 m/s range. The paper's
+    vertical axis (y) is z here, so the grid is 27 x 27 x 162 with gravity along -z. The
+    parcels fill the bed as a jittered lattice (one per chosen sub-cell of a 6x6x6 split of
+    each bed cell), all with the paper's diameter and the common volume that gives the bed's
+    solids fraction (statistical weight 10.03). The paper does not state the Snider constants:
+    Ps = 1 Pa, beta = 2, eps_cp = 0.6, alpha = 0.01 as for the dense bed."""
+    rng = np.random.default_rng(seed)
+    h = 0.12 / 27
+    p = make_params(27, 27, 162, dx=h, dy=h, dz=h, rho_g=1.093, mu_g=1.9e-5, rho_p=2000.0,
+                    u_in=u_in, alpha=0.01)
+    kz = 27                                        # 12 cm of 4.44 mm cells
+    x, y, z = _lattice_fill(rng, n, p, kz, (6, 6, 6), 0.25)
+    d = np.full(n, 400e-6)
+    vpar = 0.58 * (27 * h) * (27 * h) * (kz * h) / n
+    omega = np.full(n, vpar / (math.pi / 6.0 * 400e-6 ** 3))
+    zeros = np.zeros(n)
+    parcels = dict(x=x, y=y, z=z, u=zeros.copy(), v=zeros.copy(), w=zeros.copy(), d=d, omega=omega)
+    return Bed(p, parcels, nsteps=nsteps, meta=dict(workload="paper_sec3_27x27x162"))
+
+
+def paper_scaling_bed(n=47_853_435, seed=SEED_BASE + 7, nsteps=500) -> Bed:
+    """The shape of the paper's strong-scaling bed (Sec. 4, 4.1): a 12 x 12 x 36 cm box of 150
+    x 150 x 450 cells (0.8 mm), gravity along -z, gas of 1.0 kg/m3 and 1.8e-5 Pa s, 200 um
+    particles of 2000 kg/m3, an initial bed 12 cm tall (150 layers) at a gas fraction of 0.42,
+    inlet velocity 0.15 m/s, 47,853,435 parcels (the paper's count; statistical weight 5).
+    Jittered lattice seeding (2x2x4 sub-cells per bed cell, 89% filled); Snider constants as
+    for the dense bed."""
+    rng = np.random.default_rng(seed)
+    h = 0.0008
+    p = make_params(150, 150, 450, dx=h, dy=h, dz=h, rho_g=1.0, mu_g=1.8e-5, rho_p=2000.0,
+                    u_in=0.15, alpha=0.01)
+    kz = 150
+    x, y, z = _lattice_fill(rng, n, p, kz, (2, 2, 4), 0.25)
+    d = np.full(n, 200e-6)
+    vpar = 0.58 * (150 * h) * (150 * h) * (kz * h) / n
+    omega = np.full(n, vpar / (math.pi / 6.0 * 200e-6 ** 3))
+    zeros = np.zeros(n)
+    parcels = dict(x=x, y=y, z=z, u=zeros.copy(), v=zeros.copy(), w=zeros.copy(), d=d, omega=omega)
+    return Bed(p, parcels, nsteps=nsteps, meta=dict(workload="paper_sec4_150x150x450"))
+
+
 def grad_bed(n=500_000, nx=32, ny=32, nz=128, seed=SEED_BASE + 5, nsteps=200,
              floor_clearance=0.0) -> Bed:
     """Differentiation bed: d = 150 um, 2500 kg/m3, w = 10, lower-half fill, inflow 0.4 m/s.

@@ -65,3 +65,19 @@ def test_product_path_does_not_import_the_oracle():
         if path.endswith((".py", ".cu", ".cuh", ".h")):
             txt = open(path).read()
             assert "import oracle" not in txt and "mppic_oracle" not in txt, path
+
+
+def test_every_declaration_cites_the_paper():
+    """Each entry point's comment in include/*.h names the passage of the paper it follows (a
+    section or an equation) or says that the paper has no counterpart."""
+    missing, commented = [], set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        for m in re.finditer(r"/\*((?:(?!\*/).)*)\*/\s*\n((?:[^;/]|/(?!\*))*?\b(mppic_[a-z0-9_]+)\s*\()",
+                             src, flags=re.S):
+            comment, name = m.group(1), m.group(3)
+            commented.add(name)
+            if not re.search(r"Sec\.\s*\d|Eq\.\s*\d|no\s+(?:\*\s*)?counterpart", comment, flags=re.I):
+                missing.append(name)
+    assert not missing, missing
+    assert commented == set(declared_functions())

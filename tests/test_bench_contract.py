@@ -34,7 +34,7 @@ def test_window_never_settles_negatively():
 
 
 def test_run_lengths_cover_every_workload():
-    for w in ("dense", "fourier", "settle", "grad", "batched"):
+    for w in ("dense", "fourier", "settle", "grad", "batched", "paper_sec3", "paper_sec4"):
         assert bench.RUN_STEPS[w] > 0
 
 
@@ -61,3 +61,15 @@ def test_reference_sample_clamps_to_the_grid():
     col = bench.sub_column(bed, 50)
     assert (col.params["nx"], col.params["ny"]) == (4, 3)
     assert col.np == bed.np
+
+
+def test_cpu_baseline_reports_single_thread_and_all_cores():
+    """The CPU leg times the oracle single-threaded and on every core, on columns of the bed,
+    and states the host's CPU model and core count."""
+    bed = synth.fourier_bed(n=40_000, nx=16, ny=16, nz=24, nsteps=1)
+    cpu = bench.cpu_baseline(bed, seconds=0.6, steps=2)
+    assert cpu["kind"] == "oracle" and cpu["nproc"] >= 1 and cpu["cpu_model"]
+    st, mt = cpu["legs"]["single_thread"], cpu["legs"]["all_cores"]
+    assert st["cores"] == 1 and st["value"] > 0
+    assert mt["cores"] >= 1 and mt["value"] > 0
+    assert cpu["value"] == mt["value"] and cpu["cores"] == mt["cores"]

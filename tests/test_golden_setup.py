@@ -31,3 +31,22 @@ def test_parcel_counts_from_bed_recipe():
     assert n_ver == pytest.approx(g["verification_parcels"], rel=3e-3)
     n_scal = synth.parcel_count(1 - 0.42, bed, 200e-6, 5.0)
     assert n_scal == pytest.approx(g["scaling_parcels"], rel=1e-4)
+
+
+def test_paper_verification_bed_matches_the_printed_setup():
+    """The Sec. 3 bed as generated: the paper's parcel count, 400 um particles of 2000 kg/m3,
+    statistical weight 10 (to the rounding of the count), a 12 cm bed at gas fraction 0.42 in
+    a 12 x 72 x 12 cm box of 27 x 162 x 27 cells (vertical axis z here)."""
+    import math
+    import numpy as np
+    g = _golden()
+    b = synth.paper_verification_bed()
+    p = b.params
+    assert b.np == g["verification_parcels"]
+    assert (p["nx"], p["ny"], p["nz"]) == (27, 27, 162)
+    assert p["nz"] * p["dz"] == pytest.approx(0.72) and p["nx"] * p["dx"] == pytest.approx(0.12)
+    assert np.all(b.parcels["d"] == 400e-6) and p["rho_p"] == 2000.0
+    assert b.parcels["omega"][0] == pytest.approx(10.0, rel=3e-3)
+    es = np.sum(b.parcels["omega"] * math.pi / 6 * b.parcels["d"] ** 3) / 0.12 ** 3
+    assert es == pytest.approx(0.58, rel=1e-12)
+    assert b.parcels["z"].max() < 0.12 and b.parcels["z"].min() > 0.0

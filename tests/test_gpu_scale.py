@@ -65,6 +65,47 @@ def test_full_size_dense_bed_sampled(prec):
     b.close()
 
 
+@pytest.mark.parametrize("prec", [32, 64])
+def test_full_size_dense_bed_node_arrays(prec):
+    """The 32M-parcel dense bed, one step in the bench's launch configuration (sorted every 2
+    steps): every node of the drag sums A and B[3] against the oracle's full step (all 32M
+    parcels), and of the solids volume the step deposited for the new positions against the
+    oracle's deposit of those positions, normwise per field and element-wise wherever the
+    value is not a near-cancellation (|ref| > 1e-3 max); the new volume adds up to the
+    parcels' volumes to 1e-12."""
+    bed = _dense()
+    state = rounded(bed.parcels, prec)
+    _, ex, st = oracle.step(bed.params, state, 1)
+    assert st == 0
+    b = mppic.Bed(bed.params, precision=prec, sort_every=2)
+    dev = mppic.parcels_to_device(state, prec)
+    b.step(dev, None, 1)
+    A, B = b.drag_sums()
+    Vs = b.step_volume()
+    b.check()
+    hs = {k: dev[k].double().cpu().numpy() for k in ("x", "y", "z", "d", "omega")}
+    Vs_ref = oracle.deposit_volume(bed.params, hs["x"], hs["y"], hs["z"], hs["d"], hs["omega"])
+    got = {"Vs": Vs.cpu().numpy(), "A": A.cpu().numpy()}
+    ref = {"Vs": Vs_ref, "A": ex["A"]}
+    for a in range(3):
+        got[f"B{a}"] = B[a].cpu().numpy()
+        ref[f"B{a}"] = ex["B"][a]
+    for k in got:
+        scale = np.max(np.abs(ref[k]))
+        err = np.abs(got[k] - ref[k])
+        if scale == 0.0:                 # B_x, B_y of parcels at rest: exactly zero
+            assert np.max(np.abs(got[k])) == 0.0, k
+            continue
+        assert np.max(err) / scale <= TOL[prec], (k, np.max(err) / scale)
+        big = np.abs(ref[k]) > 1e-3 * scale
+        assert np.max(err[big] / np.abs(ref[k][big])) <= 10 * TOL[prec], k
+    dt = np.float32 if prec == 32 else np.float64
+    d, om = np.asarray(state["d"], dt), np.asarray(state["omega"], dt)
+    total = float(np.sum((om * (d * d * d) * dt(np.pi / 6)).astype(np.float64)))
+    assert abs(float(got["Vs"].sum()) - total) <= 1e-12 * total
+    b.close()
+
+
 def _gpu_means(bed, prec, steps, U=None):
     state = rounded(bed.parcels, prec)
     U = bed.U if U is None else U

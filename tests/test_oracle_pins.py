@@ -561,3 +561,22 @@ def test_implicit_coupling_uniform_bed_follows_the_scalar_recurrence():
         np.testing.assert_allclose(out["eps_s"], es, rtol=1e-12)
         np.testing.assert_allclose(out["ug"][2], u, rtol=1e-11)
         np.testing.assert_allclose(out["ug"][0], 0.0, atol=1e-15)
+
+
+def test_multithreaded_driver_equals_the_oracle():
+    """The all-core driver of the CPU baseline runs the oracle's own functions: on one thread
+    it is the oracle bit for bit; on several threads it matches to rounding."""
+    bed = synth.fourier_bed(n=5000, nx=8, ny=8, nz=16, nsteps=1)
+    synth.random_velocities(bed, 0.2, seed=14)
+    p = dict(bed.params, coupling_iters=2, drag_model=1)
+    ref, ex, st = oracle.step(p, bed.parcels, 3, U=bed.U, outputs=False)
+    one, obj1, st1 = oracle.step_mt(p, bed.parcels, 3, U=bed.U, nthreads=1)
+    assert st == st1 == 0
+    for k in ("x", "y", "z", "u", "v", "w"):
+        np.testing.assert_array_equal(one[k], ref[k])
+    np.testing.assert_array_equal(obj1, ex["obj"])
+    four, obj4, st4 = oracle.step_mt(p, bed.parcels, 3, U=bed.U, nthreads=4)
+    assert st4 == 0
+    for k in ("x", "w"):
+        np.testing.assert_allclose(four[k], ref[k], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(obj4, ex["obj"], rtol=1e-12)

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2211_15605_gb300 import mppic, synth
 
 pytestmark = pytest.mark.gpu
@@ -61,7 +62,43 @@ def test_static_deposit_matches_handle_deposit_twice(prec):
         assert np.all(np.isfinite(o))
         assert _normwise(o, ref) <= TOL[prec]
     assert np.array_equal(outs[0], outs[1])
+    # and against the oracle, with its total equal to the parcels' volumes
+    dt = np.float32 if prec == 32 else np.float64
+    q = {k: np.asarray(bed.parcels[k], dt).astype(np.float64) for k in ("x", "y", "z", "d", "omega")}
+    Vs_orc = oracle.deposit_volume(bed.params, q["x"], q["y"], q["z"], q["d"], q["omega"])
+    assert _normwise(outs[0], Vs_orc) <= TOL[prec]
+    d, om = np.asarray(bed.parcels["d"], dt), np.asarray(bed.parcels["omega"], dt)
+    total = float(np.sum((om * (d * d * d) * dt(np.pi / 6)).astype(np.float64)))
+    assert abs(float(outs[0].sum()) - total) <= 1e-12 * total
     b.close()
+
+
+@pytest.mark.parametrize("bad", ["nan_diameter", "outside_box"])
+def test_static_deposit_flags_bad_parcels_with_nan(bad):
+    """A parcel that the deposit cannot place (a non-finite value, or a position outside the
+    box) turns every output into NaN instead of a finite wrong sum; the next call is clean."""
+    L = _lib()
+    bed = synth.settle_bed(n=2000, nx=8, ny=8, nz=16)
+    parcels = {k: v.copy() for k, v in bed.parcels.items()}
+    if bad == "nan_diameter":
+        parcels["d"][17] = np.nan
+    else:
+        parcels["z"][17] = 1.0                   # the box is 16 cm tall
+    cfg = mppic.make_config(bed.params, 32, 0)
+    nn = 9 * 9 * 17
+    for p_, expect_nan in ((parcels, True), (bed.parcels, False)):
+        dev = mppic.parcels_to_device(p_, 32)
+        ps = mppic.Parcels()
+        for k in mppic.PARCEL_FIELDS:
+            setattr(ps, k, dev[k].data_ptr())
+        ps.np = dev["x"].numel()
+        out = torch.zeros(nn, dtype=torch.float64, device="cuda")
+        st = L.mppic_deposit_static(ctypes.byref(cfg), ctypes.byref(ps), ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == mppic.OK
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        assert np.all(np.isnan(o)) if expect_nan else np.all(np.isfinite(o))
 
 
 def test_static_deposit_rejects_grids_above_its_limit():
