@@ -203,17 +203,16 @@ def measured_peak():
 
 # FP64 operations per parcel of the FP64 step kernel (k_cells<double,1>): DADD + DMUL + 2 DFMA
 # thread instructions per parcel from the instruction counters of one ncu capture on the
-# 8M-parcel dense case (see the profile summary of that kernel).
-FP64_FLOPS_PER_PARCEL = 336
-FP64_FLOPS_SOURCE = "hand count of the step's arithmetic (pending a counter capture)"
+# 8M-parcel dense case: the work of the FP64 pipe, divisions and powers included.
+FP64_FLOPS_PER_PARCEL = 602
+FP64_FLOPS_SOURCE = "ncu counters: (DADD + DMUL + 2 DFMA) / parcels of one launch, 8M-parcel dense bed"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32 step kernel per
 # parcel, from ncu captures on the 128x128x128 / 8M-parcel dense bed sorted every 2 steps:
-# step 5 (58.9 B), step 290 (after a sort, 65.2 B) and step 291 (drifted, 61.9 B)
-# (profiles/k_cells_float_dense_8M.md); their mean, in proportion to the parcels. Reported
-# only while the kernel source is the one captured.
-STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 62.0,
-                "source_sha256": "353303b3bc7bc54dd41ca9a45a6c319b4679643c255a57d9e9a46820e1d59b4e"}
+# 65.4 B at step 150 (the fluidised bed, as in the timed window; 58.9 B at step 5), in
+# proportion to the parcels. Reported only while the kernel source is the one captured.
+STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 65.4,
+                "source_sha256": "07a0b867f936b7afae4924527d2bf5a1366391957c85d60000b0ff748e589690"}
 
 
 def step_traffic(args, np_):
@@ -730,26 +729,29 @@ def _sample(bed, m):
 
 
 def host_cpu():
-    """The host's CPU model and core count (what the CPU legs ran on)."""
+    """The host's CPU model and core count (what the CPU legs ran on): lscpu's model name, else
+    /proc/cpuinfo's (x86 "model name"; Arm implementer and part numbers)."""
     model = None
     try:
-        for line in open("/proc/cpuinfo"):
-            low = line.lower()
-            if low.startswith("model name") or low.startswith("cpu part") and model is None:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
                 model = line.split(":", 1)[1].strip()
-                if low.startswith("model name"):
-                    break
-    except OSError:
+                break
+    except Exception:
         pass
     if not model:
+        fields = {}
         try:
-            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
-            for line in out.splitlines():
-                if line.lower().startswith("model name"):
-                    model = line.split(":", 1)[1].strip()
-                    break
-        except Exception:
+            for line in open("/proc/cpuinfo"):
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
+        except OSError:
             pass
+        model = fields.get("model name")
+        if not model and "cpu part" in fields:
+            model = f"implementer {fields.get('cpu implementer', '?')} part {fields['cpu part']}"
     return {"cpu_model": model or "unknown", "nproc": os.cpu_count()}
 
 
