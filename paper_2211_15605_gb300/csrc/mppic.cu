@@ -102,14 +102,21 @@ struct mppic_handle {
   long long ckpt_np = 0;
   int last_nsteps = -1;
   // backward buffers
-  double* adj = nullptr;       // 6 x np: adjoint of x, y, z, u, v, w
-  double* adj_tmp = nullptr;   // 6 x np
-  double* Vb = nullptr;        // np
-  double* nadj = nullptr;      // 6 x nnode
+  void* adj = nullptr;         // 6 x np (form's type): adjoint of x, y, z, u, v, w
+  void* adj_tmp = nullptr;     // 6 x np
+  void* Vb = nullptr;          // np: adjoint of the parcel volume
+  void* nadj = nullptr;        // nnode: adjoint of the deposited volume
   int* inv = nullptr;          // np
   void* work = nullptr;        // 8 x np parcel arrays of the segment being recomputed
   void* seg = nullptr;         // ckpt_every x 6 x np saved states
-  double* theta = nullptr;     // 3 gradient accumulators + 2 height sums
+  void* adj_src = nullptr;     // 7 x np: per-parcel sources of interp^T
+  void* fcache = nullptr;      // ckpt_every x 5 x nnode: node fields of the saved states
+  double* hcache = nullptr;    // ckpt_every x 2: height sums of the saved states
+  double* part = nullptr;      // AP_ROWS x part_stride: per-block partial sums
+  long long part_stride = 0;
+  void* adj_sc = nullptr;      // the step's fixed-point multipliers (AdjScale<T>)
+  unsigned* adj_cnt = nullptr; // finished-block counter of the last-block reductions
+  double* theta = nullptr;     // 3 gradient accumulators
   long long adj_np = 0;
   int seg_len = 0;
   // profiling: event pairs recorded around each phase while enabled
@@ -746,31 +753,63 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
 }
 
 // Reverse sweep over the last checkpointed mppic_step call (see mppic_backward).
+// Per segment: the forward recompute of its states (keeping each state's node fields and
+// height sums), then the reverse steps. Every sum is integer or a fixed tree: the gradient
+// does not depend on the order in which threads run.
 template <class T>
 mppic_status backward_impl(mppic_handle* h, const double* dL, double* grad_out) {
   const long long np = h->ckpt_np;
   const int N = h->last_nsteps, K = h->ckpt_every;
   const size_t ts = h->tsize;
-  if (np > h->adj_np || h->seg_len < K) {
+  const long long nnode = h->nnode;
+  const unsigned gp = blocks(np > 0 ? np : 1, 256);
+  const unsigned gc = blocks(np > 0 ? np : 1, ADJ_CHUNK);     // chunk-tile deposits
+  const unsigned gn = blocks(nnode, 256);
+  const long long pstride = gp > gn ? gp : gn;
+  if (np > h->adj_np || h->seg_len < K || h->part_stride < pstride) {
     cudaFree(h->adj); cudaFree(h->adj_tmp); cudaFree(h->Vb); cudaFree(h->inv);
-    cudaFree(h->work); cudaFree(h->seg);
-    h->adj = h->adj_tmp = h->Vb = nullptr; h->inv = nullptr; h->work = h->seg = nullptr;
-    h->adj_np = 0; h->seg_len = 0;
+    cudaFree(h->work); cudaFree(h->seg); cudaFree(h->adj_src); cudaFree(h->fcache);
+    cudaFree(h->hcache); cudaFree(h->part);
+    h->adj = h->adj_tmp = h->Vb = nullptr;
+    h->hcache = h->part = nullptr;
+    h->inv = nullptr;
+    h->work = h->seg = h->adj_src = h->fcache = nullptr;
+    h->adj_np = 0; h->seg_len = 0; h->part_stride = 0;
     const size_t n1 = (size_t)(np > 0 ? np : 1);
-    CU(cudaMalloc(&h->adj, sizeof(double) * 6 * n1));
-    CU(cudaMalloc(&h->adj_tmp, sizeof(double) * 6 * n1));
-    CU(cudaMalloc(&h->Vb, sizeof(double) * n1));
+    CU(cudaMalloc(&h->adj, ts * 6 * n1));
+    CU(cudaMalloc(&h->adj_tmp, ts * 6 * n1));
+    CU(cudaMalloc(&h->Vb, ts * n1));
     CU(cudaMalloc(&h->inv, sizeof(int) * n1));
     CU(cudaMalloc(&h->work, ts * 8 * n1));
     CU(cudaMalloc(&h->seg, ts * 6 * n1 * (size_t)K));
-    h->adj_np = np; h->seg_len = K;
+    CU(cudaMalloc(&h->adj_src, ts * 7 * n1));
+    CU(cudaMalloc(&h->fcache, ts * 5 * (size_t)nnode * (size_t)K));
+    CU(cudaMalloc(&h->hcache, sizeof(double) * 3 * (size_t)K));
+    CU(cudaMalloc(&h->part, sizeof(double) * AP_ROWS * (size_t)pstride));
+    h->adj_np = np; h->seg_len = K; h->part_stride = pstride;
   }
-  if (!h->nadj) CU(cudaMalloc(&h->nadj, sizeof(double) * 6 * h->nnode));
-  if (!h->theta) CU(cudaMalloc(&h->theta, sizeof(double) * 5));
+  if (!h->nadj) CU(cudaMalloc(&h->nadj, ts * nnode));
+  if (!h->theta) CU(cudaMalloc(&h->theta, sizeof(double) * 3));
+  if (!h->adj_sc) {
+    CU(cudaMalloc(&h->adj_sc, sizeof(AdjScale<double>)));
+    CU(cudaMemset(h->adj_sc, 0, sizeof(AdjScale<double>)));   // no parcels: zero planes
+  }
+  if (!h->adj_cnt) {
+    CU(cudaMalloc(&h->adj_cnt, sizeof(unsigned)));
+    CU(cudaMemset(h->adj_cnt, 0, sizeof(unsigned)));
+  }
+  {
+    static bool attr = false;   // the scatter's tile exceeds the default 48 KB
+    if (!attr) {
+      CU(cudaFuncSetAttribute(k_adj_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(5 * Words<T>::n * CN * sizeof(u64))));
+      attr = true;
+    }
+  }
   cudaStream_t st = h->stream;
-  CU(cudaMemsetAsync(h->theta, 0, sizeof(double) * 5, st));
-  CU(cudaMemsetAsync(h->adj, 0, sizeof(double) * 6 * (np > 0 ? np : 1), st));
-  KParams<T> p = make_params<T>(h, &h->gas);
+  CU(cudaMemsetAsync(h->theta, 0, sizeof(double) * 3, st));
+  CU(cudaMemsetAsync(h->adj, 0, ts * 6 * (np > 0 ? np : 1), st));
+  const KParams<T> p = make_params<T>(h, &h->gas);
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   AdjWeights aw;
   aw.a_dp = dL[0] / N / area;
@@ -778,17 +817,17 @@ mppic_status backward_impl(mppic_handle* h, const double* dL, double* grad_out) 
   T* work = static_cast<T*>(h->work);
   T* wa[8];
   for (int f = 0; f < 8; ++f) wa[f] = work + (size_t)f * np;
-  const unsigned gp = blocks(np > 0 ? np : 1, 256);
-  const int nseg = (N + K - 1) / K;
-  // deposit of the state in `st6` (6 arrays) with d, omega of the work arrays, then node fields
-  auto node_fields = [&](T* const* xs) -> mppic_status {
-    CU(cudaMemsetAsync(h->acc, 0, sizeof(u64) * h->words * h->nnode, st));
-    if (np > 0) {
-      k_dep_simple<T><<<gp, 256, 0, st>>>(p, xs[0], xs[1], xs[2], wa[6], wa[7], np);
-      LAUNCHED();
-    }
-    return launch_finalize<T>(h, p, nullptr, true);
+  T* src = static_cast<T*>(h->adj_src);
+  T* fc = static_cast<T*>(h->fcache);
+  AdjScale<T>* sc = static_cast<AdjScale<T>*>(h->adj_sc);
+  const size_t plane = sizeof(u64) * h->words * (size_t)nnode;   // one accumulator plane
+  // the parameters of saved state t: its node fields in the cache
+  auto at_state = [&](int t) {
+    KParams<T> q = p;
+    for (int f = 0; f < 5; ++f) q.fld[f] = fc + ((size_t)t * 5 + f) * nnode;
+    return q;
   };
+  const int nseg = (N + K - 1) / K;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int s0 = sg * K, len = (N - s0) < K ? (N - s0) : K;
     const char* c = static_cast<const char*>(h->ckpt[sg]);
@@ -797,54 +836,71 @@ mppic_status backward_impl(mppic_handle* h, const double* dL, double* grad_out) 
       const int* tag_next = reinterpret_cast<const int*>(static_cast<const char*>(h->ckpt[sg + 1]) + ts * 8 * np);
       const int* tag_this = reinterpret_cast<const int*>(c + ts * 8 * np);
       k_tag_inverse<<<gp, 256, 0, st>>>(tag_next, np, h->inv);
-      k_adj_reorder<<<gp, 256, 0, st>>>(h->adj, h->adj_tmp, tag_this, h->inv, np);
+      k_adj_reorder<T><<<gp, 256, 0, st>>>(static_cast<T*>(h->adj), static_cast<T*>(h->adj_tmp),
+                                           tag_this, h->inv, np);
       LAUNCHED();
       std::swap(h->adj, h->adj_tmp);
     }
-    // recompute the segment's states S_s0 .. S_s0+len-1
+    // recompute the segment's states S_s0 .. S_s0+len-1 with their node fields and heights
     T* seg = static_cast<T*>(h->seg);
     for (int t = 0; t < len; ++t) {
       if (np > 0)
         CU(cudaMemcpyAsync(seg + (size_t)t * 6 * np, work, ts * 6 * np, cudaMemcpyDeviceToDevice, st));
-      if (t < len - 1) {
-        mppic_status s = node_fields(wa);
-        if (s) return s;
-        if (np > 0) {
-          k_push_simple<T><<<gp, 256, 0, st>>>(p, wa[0], wa[1], wa[2], wa[3], wa[4], wa[5], wa[6],
-                                               wa[7], np);
-          LAUNCHED();
-        }
+      const KParams<T> pt = at_state(t);
+      CU(cudaMemsetAsync(h->acc, 0, plane, st));
+      if (np > 0) {
+        k_dep_simple<T><<<gc, ADJ_THREADS, 0, st>>>(pt, wa[0], wa[1], wa[2], wa[6], wa[7], np, h->part,
+                                                    pstride, h->adj_cnt, h->hcache + 3 * t);
+        LAUNCHED();
+      } else {
+        CU(cudaMemsetAsync(h->hcache + 3 * t, 0, sizeof(double) * 3, st));
+      }
+      mppic_status s = launch_finalize<T>(h, pt, nullptr, true);
+      if (s) return s;
+      if (t < len - 1 && np > 0) {
+        k_push_simple<T><<<gp, 256, 0, st>>>(pt, wa[0], wa[1], wa[2], wa[3], wa[4], wa[5], wa[6],
+                                             wa[7], np);
+        LAUNCHED();
       }
     }
     // reverse sweep through the segment
     for (int t = len - 1; t >= 0; --t) {
       T* xs[6];
       for (int f = 0; f < 6; ++f) xs[f] = seg + ((size_t)t * 6 + f) * np;
-      mppic_status s = node_fields(xs);
-      if (s) return s;
-      CU(cudaMemsetAsync(h->theta + 3, 0, sizeof(double) * 2, st));
-      CU(cudaMemsetAsync(h->nadj, 0, sizeof(double) * 6 * h->nnode, st));
+      const KParams<T> pt = at_state(t);
+      CU(cudaMemsetAsync(h->acc, 0, plane * NQ, st));
       if (np > 0) {
-        k_height_sums<T><<<gp, 256, 0, st>>>(p, xs[2], wa[6], wa[7], np, h->theta + 3);
-        k_adj_parcel<T><<<gp, 256, 0, st>>>(p, xs[0], xs[1], xs[2], xs[3], xs[4], xs[5], wa[6], wa[7],
-                                             np, h->adj, h->adj + 3 * np, h->Vb, h->nadj,
-                                             h->theta + 3, aw, h->theta);
+        k_adj_parcel<T><<<gp, 256, 0, st>>>(pt, xs[0], xs[1], xs[2], xs[3], xs[4], xs[5], wa[6], wa[7],
+                                             np, static_cast<T*>(h->adj), static_cast<T*>(h->adj) + 3 * np,
+                                             static_cast<T*>(h->Vb), src,
+                                             h->hcache + 3 * t, aw, h->part, pstride, h->adj_cnt, sc);
+        LAUNCHED();
+        k_adj_scatter<T><<<gc, ADJ_THREADS, 5 * Words<T>::n * CN * sizeof(u64), st>>>(
+            pt, xs[0], xs[1], xs[2], np, src, sc);
         LAUNCHED();
       }
-      k_adj_node<T><<<blocks(h->nnode, 256), 256, 0, st>>>(p, h->nadj, h->theta);
+      k_adj_node<T><<<gn, 256, 0, st>>>(pt, sc, 1.0 / p.vcell, static_cast<T*>(h->nadj), h->part,
+                                        pstride);
       LAUNCHED();
       if (np > 0) {
-        k_adj_deposit<T><<<gp, 256, 0, st>>>(p, xs[0], xs[1], xs[2], wa[6], wa[7], np, h->adj,
-                                              h->Vb, h->nadj, h->theta);
-        LAUNCHED();
+        k_adj_deposit<T><<<gp, 256, 0, st>>>(pt, xs[0], xs[1], xs[2], wa[6], wa[7], np,
+                                              static_cast<T*>(h->adj), static_cast<const T*>(h->Vb),
+                                              static_cast<const T*>(h->nadj), h->part, pstride, gn,
+                                              h->adj_cnt,
+                                              h->theta);
+      } else {
+        k_adj_theta_nodes<<<1, ADJ_RED, 0, st>>>(h->part, pstride, gn, h->theta);
       }
+      LAUNCHED();
     }
   }
   double th[3];
   CU(cudaMemcpyAsync(th, h->theta, sizeof(th), cudaMemcpyDeviceToHost, st));
+  // the accumulators are left empty; the node arrays hold a recomputed state, so the next
+  // call re-deposits and finalizes every layer
+  CU(cudaMemsetAsync(h->acc, 0, plane * NQ, st));
   CU(cudaStreamSynchronize(st));
   for (int i = 0; i < 3; ++i) grad_out[i] = th[i];
-  // the node arrays now hold a recomputed state: the next call re-deposits and finalizes all
   const int zr0[4] = {1 << 30, -1, 0, h->cfg.nz};
   CU(cudaMemcpy(h->zr, zr0, sizeof(zr0), cudaMemcpyHostToDevice));
   return MPPIC_OK;
@@ -1337,7 +1393,9 @@ void mppic_destroy(mppic_handle* h) {
   cudaFree(h->tag); cudaFree(h->sorted_tag);
   for (void* c : h->ckpt) cudaFree(c);
   cudaFree(h->adj); cudaFree(h->adj_tmp); cudaFree(h->Vb); cudaFree(h->nadj); cudaFree(h->inv);
-  cudaFree(h->work); cudaFree(h->seg); cudaFree(h->theta);
+  cudaFree(h->work); cudaFree(h->seg); cudaFree(h->theta); cudaFree(h->adj_src);
+  cudaFree(h->fcache); cudaFree(h->hcache); cudaFree(h->part); cudaFree(h->adj_sc);
+  cudaFree(h->adj_cnt);
   cudaFree(h->d_poff); cudaFree(h->d_noff); cudaFree(h->d_boff); cudaFree(h->d_brick_bed);
   cudaFree(h->d_area); cudaFree(h->d_beds); cudaFree(h->wq);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
