@@ -387,18 +387,19 @@ def run_gpu(args):
 
     # end to end through the C ABI with host buffers: every step copies a parcel state in from
     # pinned host memory (all 8 arrays) and its new state and objectives back out (6 arrays +
-    # 2 doubles). The host state is the device state after a sort, in the layout of the
-    # handle's last sort (a host code that mirrors the device state sends it back in that
-    # order), so the leg runs the headline's sort schedule. Steps are pipelined over three
-    # device buffer sets: the uploads of the next steps and the downloads of the previous
-    # ones run on the copy engines (both directions at once) while step k's kernels run.
-    # Every copy and every step is bracketed by events on its own stream, so the time of each
-    # leg and their overlap are measured.
+    # 2 doubles). The host state is the device state sorted into the handle's layout (a host
+    # code that mirrors the device state sends it back in that order); sorting it again gives
+    # the same order, so every step, with or without a sort, finds the parcels in the ranges
+    # the handle holds, and the leg runs the headline's sort schedule. Steps are pipelined
+    # over three device buffer sets: the uploads of the next steps and the downloads of the
+    # previous ones run on the copy engines (both directions at once) while step k's kernels
+    # run. Every copy and every step is bracketed by events on its own stream, so the time of
+    # each leg and their overlap are measured.
     e2e = None
     if args.e2e_steps > 0:
         fields = mppic.PARCEL_FIELDS
         outs = ("x", "y", "z", "u", "v", "w")
-        b.step(parcels, gas, 1)                     # sorts if due: the state in the layout
+        b.bin(parcels, do_sort=True)                # the state in the handle's layout
         b.tune(0, args.sort_every)
         torch.cuda.synchronize()
         host = {k: parcels[k].cpu().pin_memory() for k in fields}
