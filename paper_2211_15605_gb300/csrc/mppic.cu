@@ -97,6 +97,7 @@ struct mppic_handle {
   int ckpt_every = 0;
   int* tag = nullptr;          // identity of the parcel at each caller position
   int* sorted_tag = nullptr;   // the same for the sorted copy
+  uint32_t* lperm = nullptr;   // [cap] a re-sort inside a step call: source index of each position
   long long tag_cap = 0;
   std::vector<void*> ckpt;     // per checkpoint: 8 parcel arrays then the tags
   long long ckpt_np = 0;
@@ -324,6 +325,7 @@ mppic_status upload_beds(mppic_handle* h, const mppic_gas* gas, const KParams<T>
 template <class T>
 PArrays<T> caller_arrays(const mppic_parcels* pc, int* tag = nullptr) {
   PArrays<T> a;
+  a.perm = nullptr;
   void* const src[8] = {pc->x, pc->y, pc->z, pc->u, pc->v, pc->w, pc->d, pc->omega};
   for (int f = 0; f < 8; ++f) a.a[f] = static_cast<T*>(src[f]);
   a.pid = pc->pid;
@@ -334,6 +336,7 @@ PArrays<T> caller_arrays(const mppic_parcels* pc, int* tag = nullptr) {
 template <class T>
 PArrays<T> sorted_arrays(mppic_handle* h, bool with_pid, bool with_tag = false) {
   PArrays<T> a;
+  a.perm = nullptr;
   for (int f = 0; f < 8; ++f) a.a[f] = static_cast<T*>(h->sorted[f]);
   a.pid = with_pid ? h->sorted_pid : nullptr;
   a.tag = with_tag ? h->sorted_tag : nullptr;
@@ -367,6 +370,7 @@ mppic_status ensure_capacity(mppic_handle* h, long long np, bool want_pid) {
     cudaFree(h->hist); h->hist = nullptr;
     for (int f = 0; f < 8; ++f) { cudaFree(h->sorted[f]); h->sorted[f] = nullptr; }
     cudaFree(h->sorted_pid); h->sorted_pid = nullptr;
+    cudaFree(h->lperm); h->lperm = nullptr;
     h->cap = 0;
     long long nblk = (cap + SORT_TILE - 1) / SORT_TILE;
     for (int i = 0; i < 2; ++i) {
@@ -376,6 +380,7 @@ mppic_status ensure_capacity(mppic_handle* h, long long np, bool want_pid) {
     }
     CU(cudaMalloc(&h->hist, sizeof(uint32_t) * 256 * (nblk > 0 ? nblk : 1)));
     for (int f = 0; f < 8; ++f) CU(cudaMalloc(&h->sorted[f], h->tsize * cap));
+    CU(cudaMalloc(&h->lperm, sizeof(uint32_t) * cap));
     h->cap = cap;
   }
   if (want_pid && !h->sorted_pid) CU(cudaMalloc(&h->sorted_pid, sizeof(int) * h->cap));
@@ -387,7 +392,7 @@ mppic_status ensure_capacity(mppic_handle* h, long long np, bool want_pid) {
 template <class T>
 mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays<T> cur,
                                bool keys_ready = false, bool local = false,
-                               const mppic_gas* gas = nullptr) {
+                               const mppic_gas* gas = nullptr, bool perm_only = false) {
   const long long np = pc->np;
   mppic_status s = ensure_capacity(h, np, pc->pid != nullptr);
   if (s) return s;
@@ -426,7 +431,7 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
       k_rs_build<T><<<(unsigned)nb, RS_THREADS, 0, st>>>(
           cur, sorted_arrays<T>(h, cur.pid != nullptr, cur.tag != nullptr), h->rs_start,
           h->rs_count, h->rs_far, h->keys[1], h->bcell[0], h->vals[0], h->bcell[1], h->cstart,
-          h->cellmap);
+          h->cellmap, perm_only ? h->lperm : nullptr);
       LAUNCHED();
       ph.launched(keys_ready ? 5 : 6);
       h->order_np = np;
@@ -520,26 +525,26 @@ mppic_status clear_volume_accumulator(mppic_handle* h) {
 }
 
 // One cell kernel instance: its shared-memory attribute and resident CTAs are set up once.
-template <class T, int MODE, int DRAG, bool BATCH>
+template <class T, int MODE, int DRAG, bool BATCH, bool PERM>
 mppic_status cell_kernel_setup(mppic_handle* h, int* resident) {
   static bool done = false;
   static int res = 0;
   if (!done) {
     const size_t sm = CellSmem<T>::bytes;
-    CU(cudaFuncSetAttribute(k_cells<T, MODE, DRAG, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)sm));
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, k_cells<T, MODE, DRAG, BATCH>, BCELLS, sm));
+    CU(cudaFuncSetAttribute(k_cells<T, MODE, DRAG, BATCH, PERM>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, k_cells<T, MODE, DRAG, BATCH, PERM>, BCELLS, sm));
     done = true;
   }
   *resident = res;
   return MPPIC_OK;
 }
 
-template <class T, int MODE, int DRAG, bool BATCH>
+template <class T, int MODE, int DRAG, bool BATCH, bool PERM>
 mppic_status launch_cells_b(mppic_handle* h, const KParams<T>& p, PArrays<T> src, PArrays<T> dst,
                             int* cell_out, long long np, const KParams<T>* beds, uint32_t* key_out) {
   int resident = 0;
-  mppic_status s = cell_kernel_setup<T, MODE, DRAG, BATCH>(h, &resident);
+  mppic_status s = cell_kernel_setup<T, MODE, DRAG, BATCH, PERM>(h, &resident);
   if (s) return s;
   if (h->nbricks == 0) return MPPIC_OK;
   // persistent grid: the CTAs that fit on the GPU at once (or grid_factor per SM)
@@ -549,18 +554,24 @@ mppic_status launch_cells_b(mppic_handle* h, const KParams<T>& p, PArrays<T> src
   CU(cudaMemsetAsync(h->wq, 0, sizeof(unsigned long long), h->stream));
   Phase ph(h, MODE == MODE_VOLUME ? PH_DEPOSIT : MODE == MODE_STEP ? PH_STEP : PH_COUPLE);
   ph.launched();
-  k_cells<T, MODE, DRAG, BATCH><<<(unsigned)grid, BCELLS, CellSmem<T>::bytes, h->stream>>>(
+  k_cells<T, MODE, DRAG, BATCH, PERM><<<(unsigned)grid, BCELLS, CellSmem<T>::bytes, h->stream>>>(
       p, beds, h->d_brick_bed, h->nbricks, h->wq, src, dst, cell_out, key_out, h->obj_part, np);
   LAUNCHED();
   return MPPIC_OK;
 }
 
-// A batch (beds != NULL) takes the instance that reads each bed's parameters from `beds`.
+// A batch (beds != NULL) takes the instance that reads each bed's parameters from `beds`;
+// src.perm set (a step after a sort that wrote only the permutation) the instance that reads
+// its parcels through it.
 template <class T, int MODE, int DRAG>
 mppic_status launch_cells_t(mppic_handle* h, const KParams<T>& p, PArrays<T> src, PArrays<T> dst,
                             int* cell_out, long long np, const KParams<T>* beds, uint32_t* key_out) {
-  return beds ? launch_cells_b<T, MODE, DRAG, true>(h, p, src, dst, cell_out, np, beds, key_out)
-              : launch_cells_b<T, MODE, DRAG, false>(h, p, src, dst, cell_out, np, beds, key_out);
+  if constexpr (MODE == MODE_STEP)
+    if (src.perm)
+      return beds ? launch_cells_b<T, MODE, DRAG, true, true>(h, p, src, dst, cell_out, np, beds, key_out)
+                  : launch_cells_b<T, MODE, DRAG, false, true>(h, p, src, dst, cell_out, np, beds, key_out);
+  return beds ? launch_cells_b<T, MODE, DRAG, true, false>(h, p, src, dst, cell_out, np, beds, key_out)
+              : launch_cells_b<T, MODE, DRAG, false, false>(h, p, src, dst, cell_out, np, beds, key_out);
 }
 
 // mode: MODE_VOLUME, MODE_STEP or MODE_DRAG; the Wen-Yu-only instance unless a bed names
@@ -690,11 +701,30 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   s = launch_cells<T>(h, MODE_VOLUME, p, src, src, nullptr, pc->np, beds);   // Vs of the current positions
   if (s) return s;
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
+  // A re-sort inside the call may leave the values where they are and only write the
+  // permutation, which the step reads its parcels through, writing them to the other buffer
+  // (the handle's copy, or the caller's arrays if the values are in the copy); a step without
+  // a sort writes the caller's arrays. Taken where no identity array travels with the parcels
+  // and no gas iteration reads them before the step.
+  const bool perm_sort = !ck && !pc->pid && h->cfg.coupling_iters == 0;
+  const PArrays<T> caller = dst;
+  bool in_copy = false;                          // the current values are in the handle's copy
   for (int it = 0; it < nsteps; ++it) {
+    dst = caller;
     if (it > 0 && sort_due(h->step_counter + it)) {
-      s = sort_into_scratch<T>(h, pc, dst, true, true, gas);   // keys from the previous step
-      if (s) return s;
-      src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
+      if (perm_sort) {
+        s = sort_into_scratch<T>(h, pc, src, true, true, gas, true);   // keys from the previous step
+        if (s) return s;
+        if (!in_copy) dst = sorted_arrays<T>(h, false, false);
+        in_copy = !in_copy;
+        src.perm = h->lperm;
+      } else {
+        s = sort_into_scratch<T>(h, pc, caller, true, true, gas);    // keys from the previous step
+        if (s) return s;
+        src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
+      }
+    } else {
+      in_copy = false;
     }
     if (ck && it % h->ckpt_every == 0) {
       s = save_checkpoint<T>(h, it / h->ckpt_every, src, np);
@@ -729,6 +759,10 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
       LAUNCHED();
     }
   }
+  if (in_copy && np > 0)                         // the last step wrote the handle's copy
+    for (int f = 0; f < 8; ++f)
+      CU(cudaMemcpyAsync(caller.a[f], h->sorted[f], h->tsize * np, cudaMemcpyDeviceToDevice, h->stream));
+  dst = caller;
   if (nsteps > 0) {              // the last step's drag sums, complete, for the drag-sum output
     s = launch_drag_fold<T>(h, p, beds);
     if (s) return s;
@@ -985,6 +1019,9 @@ mppic_status prepare_capture(mppic_handle* h, const mppic_parcels* pc, const mpp
   s = launch_cells<T>(h, MODE_VOLUME, p, none, none, nullptr, 0, beds);
   if (!s) s = launch_cells<T>(h, MODE_STEP, p, none, none, nullptr, 0, beds);
   if (!s) s = launch_cells<T>(h, MODE_DRAG, p, none, none, nullptr, 0, beds);
+  PArrays<T> none_perm = none;                 // the instance that reads through a permutation
+  none_perm.perm = reinterpret_cast<const uint32_t*>(h->cstart);
+  if (!s) s = launch_cells<T>(h, MODE_STEP, p, none_perm, none, nullptr, 0, beds);
   h->nbricks = saved;
   if (s) return s;
   CU(cudaStreamSynchronize(h->stream));
@@ -1390,7 +1427,7 @@ void mppic_destroy(mppic_handle* h) {
   for (int f = 0; f < 8; ++f) cudaFree(h->sorted[f]);
   cudaFree(h->sorted_pid);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
-  cudaFree(h->tag); cudaFree(h->sorted_tag);
+  cudaFree(h->tag); cudaFree(h->sorted_tag); cudaFree(h->lperm);
   for (void* c : h->ckpt) cudaFree(c);
   cudaFree(h->adj); cudaFree(h->adj_tmp); cudaFree(h->Vb); cudaFree(h->nadj); cudaFree(h->inv);
   cudaFree(h->work); cudaFree(h->seg); cudaFree(h->theta); cudaFree(h->adj_src);

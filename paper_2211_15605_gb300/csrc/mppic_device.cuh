@@ -398,6 +398,8 @@ struct PArrays {
   T* a[8];        // x y z u v w d omega
   int* pid;       // caller's identity array (optional)
   int* tag;       // the handle's identity array while checkpointing (optional)
+  const uint32_t* perm;   // (step kernel reads only) the parcel of layout position q is at
+                          // index perm[q] of a[] (a sort that moved no values); else q
 };
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -908,7 +910,7 @@ template <> struct CellOccupancy<double> { static constexpr int ctas = 1; };
 // BATCH: the parameters of each brick's bed come from `beds` (copied to shared memory when
 // the bed changes); otherwise from p0, which the kernel reads in place from its constant
 // parameter space (no copy, no per-use shared-memory load).
-template <class T, int MODE, int DRAG, bool BATCH>
+template <class T, int MODE, int DRAG, bool BATCH, bool PERM = false>
 __global__ void __launch_bounds__(BCELLS, CellOccupancy<T>::ctas)
 k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ beds,
         const int* __restrict__ brick_bed, long long total_bricks,
@@ -999,26 +1001,56 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   // Level r's parcel values are copied into this thread's slots of stage r % PSTAGES
   // PSTAGES-1 levels ahead of their use; each thread reads only its own slots, so it waits
   // only for its own copies. Every iteration commits one group (possibly empty).
+  // PERM (the step after a sort that wrote only the permutation): the values of layout
+  // position q are read from index src.perm[q]; each prefetch loads the next level's index,
+  // so that its latency is covered by one iteration.
   int pf_off = off;                              // first position of the next level to prefetch
-  auto prefetch = [&](int lv) {
+  uint32_t pf_src = 0;                           // PERM: this thread's index in that level
+  auto perm_at = [&](int lv, int base) -> uint32_t {
+    const bool a = n > lv;
+    const unsigned bl = __ballot_sync(FULL, a);
+    return a ? __ldg(src.perm + base + __popc(bl & below)) : 0u;
+  };
+  auto prefetch = [&](int lv, bool next) {
     const bool a = n > lv;
     const unsigned bl = __ballot_sync(FULL, a);
     if (a) {
       const int q = pf_off + __popc(bl & below);
+      const uint32_t sq = PERM ? pf_src : (uint32_t)q;
       T* slot = pre + (lv % PSTAGES) * 8 * BCELLS + tid;
 #pragma unroll
       for (int f = 0; f < 8; ++f)
-        if (MODE != MODE_VOLUME || f < 3 || f >= 6) cp_async(slot + f * BCELLS, src.a[f] + q);
+        if (MODE != MODE_VOLUME || f < 3 || f >= 6) cp_async(slot + f * BCELLS, src.a[f] + sq);
     }
     pf_off += __popc(bl);
+    if (PERM && next && lv + 1 < nmax) pf_src = perm_at(lv + 1, pf_off);
   };
+  if (PERM) {                    // the first PSTAGES levels' indices, all loads in flight at once
+    uint32_t pv[PSTAGES];
+    int base = pf_off;
 #pragma unroll
-  for (int lv = 0; lv < PSTAGES - 1; ++lv) {
-    if (lv < nmax) prefetch(lv);
-    cp_async_commit();
+    for (int lv = 0; lv < PSTAGES; ++lv) {
+      const bool a = n > lv;
+      const unsigned bl = __ballot_sync(FULL, a);
+      pv[lv] = a ? __ldg(src.perm + base + __popc(bl & below)) : 0u;
+      base += __popc(bl);
+    }
+#pragma unroll
+    for (int lv = 0; lv < PSTAGES - 1; ++lv) {
+      pf_src = pv[lv];
+      if (lv < nmax) prefetch(lv, false);
+      cp_async_commit();
+    }
+    pf_src = pv[PSTAGES - 1];
+  } else {
+#pragma unroll
+    for (int lv = 0; lv < PSTAGES - 1; ++lv) {
+      if (lv < nmax) prefetch(lv, false);
+      cp_async_commit();
+    }
   }
   for (int r = 0; r < nmax; ++r) {
-    if (r + PSTAGES - 1 < nmax) prefetch(r + PSTAGES - 1);
+    if (r + PSTAGES - 1 < nmax) prefetch(r + PSTAGES - 1, true);
     cp_async_commit();
     cp_async_wait<PSTAGES - 1>();
     const bool act = n > r;
@@ -1116,8 +1148,11 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
           dst.a[3][q] = up[0]; dst.a[4][q] = up[1]; dst.a[5][q] = up[2];
           if (copy_ro) {
             dst.a[6][q] = d; dst.a[7][q] = om;
-            if (src.pid) dst.pid[q] = src.pid[q];
-            if (src.tag) dst.tag[q] = src.tag[q];
+            if (src.pid || src.tag) {
+              const uint32_t sq = PERM ? __ldg(src.perm + q) : (uint32_t)q;
+              if (src.pid) dst.pid[q] = src.pid[sq];
+              if (src.tag) dst.tag[q] = src.tag[sq];
+            }
           }
           if (cell_out) cell_out[q] = cell_id(p, cn.i, cn.j, cn.k);
           if (key_out) key_out[q] = (uint32_t)(p.bbase * BCELLS) + brick_key(p, cn.i, cn.j, cn.k);

@@ -18,7 +18,9 @@
 //                 the bucket, in any order;
 //   k_rs_build    per destination brick: if far parcels arrived, sort the bucket by source
 //                 index (LSD passes in the CTA); then a stable counting pass by cell gives
-//                 the cell starts and the permutation, and level_layout moves the parcels.
+//                 the cell starts and the permutation, and level_layout moves the parcels
+//                 (or, inside a step call, writes only the permutation, which the next
+//                 step kernel reads its parcels through).
 //
 // The result is exactly the stable sort of the current order by key, whatever that order
 // is (a bucket in source order, then a stable pass by cell); locality only decides the
@@ -124,6 +126,13 @@ k_rs_hist(const uint32_t* __restrict__ key, const int* __restrict__ cstart,
       for (int j = 0; j < RS_U; ++j) {
         const bool ok = i0 + j * 32 + lane < hi;
         const uint32_t B = kk[j] / BCELLS;
+        const bool own = !ok || B == (uint32_t)b;
+        if (__all_sync(FULL, own)) {             // the common case: no lane left the brick
+          const unsigned bl = __ballot_sync(FULL, ok);
+          if (lane == 0) s_w[warp][13] += __popc(bl);
+          __syncwarp();
+          continue;
+        }
         const int slot = !ok ? -2 : (B == (uint32_t)b ? 13 : rs_slot(g, bx, by, bz, B));
         const unsigned m = match_bits<5>((unsigned)(slot + 2));
         if (slot >= 0) {
@@ -243,6 +252,20 @@ k_rs_scatter(const uint32_t* __restrict__ key, const int* __restrict__ cstart,
         const int q = i0 + j * 32 + lane;
         const bool ok = q < hi;
         const uint32_t B = kk[j] / BCELLS;
+        const bool own = !ok || B == (uint32_t)b;
+        if (__all_sync(FULL, own)) {             // the common case: the warp's run is contiguous
+          const unsigned bl = __ballot_sync(FULL, ok);
+          const int base = s_w[warp][13];
+          if (ok) {
+            const int pos = base + __popc(bl & below);
+            bsrc[pos] = (uint32_t)q;
+            bcell[pos] = (uint8_t)(kk[j] % BCELLS);
+          }
+          __syncwarp();
+          if (lane == 0) s_w[warp][13] = base + __popc(bl);
+          __syncwarp();
+          continue;
+        }
         const int slot = !ok ? -2 : (B == (uint32_t)b ? 13 : rs_slot(g, bx, by, bz, B));
         const unsigned m = match_bits<5>((unsigned)(slot + 2));
         if (slot >= -1) {
@@ -298,11 +321,8 @@ __device__ void rs_pass(const uint32_t* in_s, const uint8_t* in_c, uint32_t* out
       if (i < hi) dd[j] = Dig::cell_only ? dig(0u, in_c[i]) : dig(in_s[i], in_c[i]);
     }
 #pragma unroll
-    for (int j = 0; j < RS_U; ++j) {
-      const unsigned m = match_bits<8>((unsigned)dd[j] & 255u) & __ballot_sync(FULL, dd[j] >= 0);
-      if (dd[j] >= 0 && (m & below) == 0) ps.w[warp][dd[j]] += __popc(m);
-      __syncwarp();
-    }
+    for (int j = 0; j < RS_U; ++j)               // integer counts: their order does not matter
+      if (dd[j] >= 0) atomicAdd(&ps.w[warp][dd[j]], 1);
   }
   __syncthreads();
   {                                              // digit t: warps' offsets, then digit start
@@ -357,7 +377,7 @@ __global__ void __launch_bounds__(RS_THREADS, RsOccupancy<T>::ctas)
 k_rs_build(PArrays<T> src, PArrays<T> dst, const int* __restrict__ bstart,
            const int* __restrict__ bcount, const int* __restrict__ far_cnt, uint32_t* bsrc,
            uint8_t* bcell, uint32_t* tsrc, uint8_t* tcell, int* __restrict__ cstart,
-           uint8_t* __restrict__ cellmap) {
+           uint8_t* __restrict__ cellmap, uint32_t* __restrict__ lperm) {
   __shared__ union {
     RsPass ps;
     LevelSmem ls;
@@ -432,7 +452,7 @@ k_rs_build(PArrays<T> src, PArrays<T> dst, const int* __restrict__ bstart,
   if (t == 0) s_cs[BCELLS] = n;
   cstart[k0 + t] = bs + cs;
   __syncthreads();
-  level_layout<T>(src, dst, k0, bs, s_cs, perm, cellmap, u.ls);
+  level_layout<T>(src, dst, k0, bs, s_cs, perm, cellmap, u.ls, lperm);
 }
 
 }  // namespace mppic

@@ -364,12 +364,14 @@ __device__ __forceinline__ void rank_cells(int cnt, int big, LevelSmem& ls) {
 
 // One CTA (BCELLS threads) lays out brick k0 / BCELLS: its parcels occupy sorted positions
 // [bs, bs + cs[BCELLS]); cs (shared) holds each cell's first position relative to bs, and
-// perm[i] the source index of relative sorted position i (shared or global).
+// perm[i] the source index of relative sorted position i (shared or global). With lperm,
+// only the source index of every layout position is written (lperm[q]); the values stay
+// where they are and the next step kernel reads them through lperm.
 template <class T>
 __device__ __forceinline__ void level_layout(const PArrays<T>& src, const PArrays<T>& dst,
                                              long long k0, int bs, const int* cs,
                                              const uint32_t* perm, uint8_t* __restrict__ cellmap,
-                                             LevelSmem& ls) {
+                                             LevelSmem& ls, uint32_t* __restrict__ lperm = nullptr) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (cs[BCELLS] == 0) {                         // an empty brick: own order (never ranked)
     cellmap[k0 + t] = (uint8_t)t;
@@ -430,6 +432,13 @@ __device__ __forceinline__ void level_layout(const PArrays<T>& src, const PArray
       q[l] = acc + __popc(bl & below);
       acc += __popc(bl);
       si[l] = a[l] ? perm[c0 + r + l] : 0u;
+    }
+    if (lperm) {                                 // uniform: the permutation only
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+        if (a[l]) lperm[q[l]] = si[l];
+      off = acc;
+      continue;
     }
     T v[L][8];
     int ip[L], ig[L];

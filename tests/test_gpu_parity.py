@@ -351,6 +351,44 @@ def test_few_steps_sort_schedules(prec):
 
 
 @pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("every,nsteps", [(1, 5), (2, 6), (2, 7), (3, 7)])
+def test_permutation_sorts_equal_gathered_sorts(prec, every, nsteps):
+    """A re-sort inside a step call writes only the permutation when no identity array travels
+    with the parcels (the next step reads its parcels through it into the other buffer); with
+    a pid array it moves the values. Both give the same layout and the same arithmetic, so the
+    caller's arrays, objectives and drag sums must agree bit for bit, for sort periods and step
+    counts that leave the values in either buffer at the end of the call."""
+    bed = synth.settle_bed(n=20_000, nx=16, ny=16, nz=32)
+    synth.random_velocities(bed, 0.5, seed=10)
+    bed.params["dt"] = 5e-3          # parcels cross cells between sorts
+    outs = []
+    for with_pid in (True, False):
+        b = mppic.Bed(bed.params, precision=prec, sort_every=every)
+        dev = mppic.parcels_to_device(bed.parcels, prec, with_pid=with_pid)
+        obj = b.step(dev, None, nsteps)
+        obj2 = b.step(dev, None, 2)              # a second call from the layout left behind
+        A, B = b.drag_sums()
+        b.check()
+        outs.append([host(dev[k]) for k in mppic.PARCEL_FIELDS] + [host(obj), host(obj2), host(A), host(B)])
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("every", [1, 2])
+def test_permutation_sorts_equal_gathered_sorts_batch(every):
+    beds = synth.batched_beds(nbeds=6, np_lo=2_000, np_hi=20_000, seed=23)
+    outs = []
+    for with_pid in (True, False):
+        dev, gas = mppic.concat_beds(beds, 32, with_pid=with_pid)
+        b = mppic.Batch([x.params for x in beds], [x.np for x in beds], precision=32, sort_every=every)
+        obj = b.step(dev, gas, 5)
+        b.check()
+        outs.append([host(dev[k]) for k in mppic.PARCEL_FIELDS] + [host(obj)])
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
 def test_step_is_deterministic(prec):
     bed = synth.settle_bed(n=40_000, nx=16, ny=16, nz=32)
     synth.random_velocities(bed, 0.5, seed=9)
