@@ -211,11 +211,19 @@ FP64_FLOPS_SOURCE = "ncu counters: (DADD + DMUL + 2 DFMA) / parcels of one launc
 # parcel, from ncu captures on the 128x128x128 / 8M-parcel dense bed sorted every 2 steps:
 # 65.4 B at step 150 (the fluidised bed, as in the timed window; 58.9 B at step 5), in
 # proportion to the parcels. Reported only while the kernel source is the one captured.
-STEP_TRAFFIC = {"workload": "dense", "precision": 32, "bytes_per_parcel": 65.4,
-                "source_sha256": "07a0b867f936b7afae4924527d2bf5a1366391957c85d60000b0ff748e589690"}
+STEP_TRAFFIC = {"workload": "dense", "precision": 32,
+                # DRAM bytes per parcel of one launch of each step-kernel instance, ncu on the
+                # 8M-parcel dense bed at step 150: a step that updates the values in place, and
+                # a step after a sort that reads them through the sort's permutation
+                "in_place_bytes_per_parcel": 61.9, "perm_bytes_per_parcel": 70.5,
+                "source_sha256": "8e8b305067b0a525973af8e9fb183cd3965435ff901e6c7a69f4fe8d70f74ca9"}
 
 
-def step_traffic(args, np_):
+def step_traffic(args, np_, start):
+    """Measured DRAM bytes per step launch over the timed window, from the per-instance
+    captures (the call's first step after a sort at its start reads the sorted copy and
+    writes the caller's arrays: the in-place figure plus its two more written values), or
+    None if the kernel source has changed since the captures."""
     import hashlib
     src = os.path.join(ROOT, "paper_2211_15605_gb300", "csrc", "mppic_device.cuh")
     with open(src, "rb") as f:
@@ -223,16 +231,50 @@ def step_traffic(args, np_):
     t = STEP_TRAFFIC
     if args.workload != t["workload"] or args.precision != t["precision"] or sha != t["source_sha256"]:
         return None
-    return int(round(t["bytes_per_parcel"] * np_))
+    due = lambda k: args.sort_every > 0 and k % args.sort_every == 0
+    per = []
+    for it in range(args.steps):
+        if it == 0:
+            per.append(t["in_place_bytes_per_parcel"] + (8 if due(start) else 0))
+        elif due(start + it):
+            per.append(t["perm_bytes_per_parcel"])
+        else:
+            per.append(t["in_place_bytes_per_parcel"])
+    return int(round(sum(per) / len(per) * np_))
 
-def bytes_per_launch(np_, active_bricks, precision):
-    """Algorithmic DRAM bytes of one fused step launch: every parcel's state read once
-    (x,y,z,u,v,w,d,w: 8 values) and written once (x,y,z,u,v,w: 6 values), plus per occupied
-    brick its node-field tile read once (5 fields x 405 nodes) and its five accumulator
-    planes written once (405 nodes)."""
+
+def state_bytes_per_parcel(precision, sort_every, start, nsteps, perm_sorts=True):
+    """Parcel-state bytes per parcel of the step launches of one mppic_step call of nsteps
+    steps starting at step `start`, averaged over the launches, as the library schedules
+    them: a step updates the values where they are (8 values read, x,y,z,u,v,w written:
+    14 values); the step after a sort at the call start reads the sorted copy and writes the
+    caller's arrays (16 values); the step after a sort inside the call reads the values
+    through the sort's permutation (a 4-byte index) and writes all 8 to the other buffer
+    (16 values + 4 B), unless perm_sorts is off (a pid or checkpoint travels with the
+    parcels: the sort moved the values, the step reads the copy, 16 values)."""
+    t = 4 if precision == 32 else 8
+    due = lambda k: sort_every > 0 and k % sort_every == 0
+    per = []
+    for it in range(nsteps):
+        if it == 0:
+            per.append(16 * t if due(start) else 14 * t)
+        elif due(start + it):
+            per.append(16 * t + (4 if perm_sorts else 0))
+        else:
+            per.append(14 * t)
+    return sum(per) / max(len(per), 1)
+
+
+def bytes_per_launch(np_, active_bricks, precision, per_parcel=None):
+    """Algorithmic DRAM bytes of one fused step launch: every parcel's state read once and
+    written once (per_parcel bytes; default the in-place step: x,y,z,u,v,w,d,w read, 8
+    values, and x,y,z,u,v,w written, 6 values), plus per occupied brick its node-field tile
+    read once (5 fields x 405 nodes) and its five accumulator planes written once (405
+    nodes)."""
     t = 4 if precision == 32 else 8
     words = 1 if precision == 32 else 2
-    per_parcel = 14 * t
+    if per_parcel is None:
+        per_parcel = 14 * t
     per_brick = 405 * (5 * t + 5 * 8 * words)
     return np_ * per_parcel + active_bricks * per_brick
 
@@ -293,7 +335,8 @@ def time_bed(bed, precision, sort_every, steps, pre, stream, dev, barrier, param
     peak, _ = measured_peak()
     n_step = max(pr["launches"]["step"], 1)
     step_ms = pr["ms"]["step"] / n_step
-    bpl = bytes_per_launch(bed.np, pr["active_bricks"], precision)
+    bpl = bytes_per_launch(bed.np, pr["active_bricks"], precision,
+                           state_bytes_per_parcel(precision, sort_every, pre, steps))
     out = {"value": bed.np * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
            "steps": steps, "timed_steps": [pre, pre + steps], "sort_every": sort_every,
            "phase_ms_per_step": {k: round(v / steps, 4) for k, v in pr["ms"].items() if v > 0},
@@ -365,11 +408,12 @@ def run_gpu(args):
     peak, peak_kind = measured_peak()
     n_step = max(prof["launches"]["step"], 1)
     step_ms = prof["ms"]["step"] / n_step
-    bpl = bytes_per_launch(bed.np, prof["active_bricks"], args.precision)
+    bpl = bytes_per_launch(bed.np, prof["active_bricks"], args.precision,
+                           state_bytes_per_parcel(args.precision, args.sort_every, pre, args.steps))
     achieved = bpl / (step_ms / 1e3) / 1e9
     shares = {k: round(v / max(sum(prof["ms"].values()), 1e-9), 4) for k, v in prof["ms"].items()}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": step_traffic(args, bed.np),
+                "frac": round(achieved / peak, 4), "traffic": step_traffic(args, bed.np, pre),
                 "kernel": "k_cells<float,1> (fused interp/drag/push/deposit)" if args.precision == 32
                 else "k_cells<double,1>", "peak_kind": peak_kind + " (hbm_gbs copy burst)",
                 "bytes_per_launch": bpl, "ms_per_launch": round(step_ms, 5), "phase_ms": prof["ms"],
@@ -638,7 +682,8 @@ def batched_leg(args, steps, with_cpu=True):
     peak, peak_kind = measured_peak()
     n_step = max(prof["launches"]["step"], 1)
     step_ms = prof["ms"]["step"] / n_step
-    bpl = bytes_per_launch(total, prof["active_bricks"], args.precision)
+    bpl = bytes_per_launch(total, prof["active_bricks"], args.precision,
+                           state_bytes_per_parcel(args.precision, period, 0, period))
     achieved = bpl / (step_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,

@@ -704,18 +704,20 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   // A re-sort inside the call may leave the values where they are and only write the
   // permutation, which the step reads its parcels through, writing them to the other buffer
   // (the handle's copy, or the caller's arrays if the values are in the copy); a step without
-  // a sort writes the caller's arrays. Taken where no identity array travels with the parcels
+  // a sort updates the values where they are, and the copy's values go back to the caller's
+  // arrays once, after the last step. Taken where no identity array travels with the parcels
   // and no gas iteration reads them before the step.
   const bool perm_sort = !ck && !pc->pid && h->cfg.coupling_iters == 0;
   const PArrays<T> caller = dst;
+  const PArrays<T> copy = sorted_arrays<T>(h, false, false);
   bool in_copy = false;                          // the current values are in the handle's copy
   for (int it = 0; it < nsteps; ++it) {
-    dst = caller;
+    if (it > 0) dst = in_copy ? copy : caller;   // (step 0 writes the caller's arrays)
     if (it > 0 && sort_due(h->step_counter + it)) {
       if (perm_sort) {
         s = sort_into_scratch<T>(h, pc, src, true, true, gas, true);   // keys from the previous step
         if (s) return s;
-        if (!in_copy) dst = sorted_arrays<T>(h, false, false);
+        dst = in_copy ? caller : copy;
         in_copy = !in_copy;
         src.perm = h->lperm;
       } else {
@@ -723,8 +725,6 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
         if (s) return s;
         src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
       }
-    } else {
-      in_copy = false;
     }
     if (ck && it % h->ckpt_every == 0) {
       s = save_checkpoint<T>(h, it / h->ckpt_every, src, np);
