@@ -221,9 +221,7 @@ STEP_TRAFFIC = {"workload": "dense", "precision": 32,
 
 def step_traffic(args, np_, start):
     """Measured DRAM bytes per step launch over the timed window, from the per-instance
-    captures (the call's first step after a sort at its start reads the sorted copy and
-    writes the caller's arrays: the in-place figure plus its two more written values), or
-    None if the kernel source has changed since the captures."""
+    captures, or None if the kernel source has changed since the captures."""
     import hashlib
     src = os.path.join(ROOT, "paper_2211_15605_gb300", "csrc", "mppic_device.cuh")
     with open(src, "rb") as f:
@@ -232,34 +230,25 @@ def step_traffic(args, np_, start):
     if args.workload != t["workload"] or args.precision != t["precision"] or sha != t["source_sha256"]:
         return None
     due = lambda k: args.sort_every > 0 and k % args.sort_every == 0
-    per = []
-    for it in range(args.steps):
-        if it == 0:
-            per.append(t["in_place_bytes_per_parcel"] + (8 if due(start) else 0))
-        elif due(start + it):
-            per.append(t["perm_bytes_per_parcel"])
-        else:
-            per.append(t["in_place_bytes_per_parcel"])
+    per = [t["perm_bytes_per_parcel"] if due(start + it) else t["in_place_bytes_per_parcel"]
+           for it in range(args.steps)]
     return int(round(sum(per) / len(per) * np_))
 
 
 def state_bytes_per_parcel(precision, sort_every, start, nsteps, perm_sorts=True):
     """Parcel-state bytes per parcel of the step launches of one mppic_step call of nsteps
     steps starting at step `start`, averaged over the launches, as the library schedules
-    them: a step updates the values where they are (8 values read, x,y,z,u,v,w written:
-    14 values); the step after a sort at the call start reads the sorted copy and writes the
-    caller's arrays (16 values); the step after a sort inside the call reads the values
-    through the sort's permutation (a 4-byte index) and writes all 8 to the other buffer
-    (16 values + 4 B), unless perm_sorts is off (a pid or checkpoint travels with the
-    parcels: the sort moved the values, the step reads the copy, 16 values)."""
+    them (the call follows an earlier call on the same handle): a step updates the values
+    where they are (8 values read, x,y,z,u,v,w written: 14 values); the step after a sort
+    reads the values through the sort's permutation (a 4-byte index) and writes all 8 to the
+    other buffer (16 values + 4 B), unless perm_sorts is off (a pid or checkpoint travels
+    with the parcels: the sort moved the values, the step reads the copy, 16 values)."""
     t = 4 if precision == 32 else 8
     due = lambda k: sort_every > 0 and k % sort_every == 0
     per = []
     for it in range(nsteps):
-        if it == 0:
-            per.append(16 * t if due(start) else 14 * t)
-        elif due(start + it):
-            per.append(16 * t + (4 if perm_sorts else 0))
+        if due(start + it):
+            per.append(16 * t + 4 if perm_sorts else 16 * t)
         else:
             per.append(14 * t)
     return sum(per) / max(len(per), 1)

@@ -683,14 +683,28 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   }
   PArrays<T> dst = caller_arrays<T>(pc, ck ? h->tag : nullptr);
   PArrays<T> src = dst;
+  const PArrays<T> caller = dst;
   const int every = h->cfg.sort_every;
   auto sort_due = [&](long long step) { return every > 0 && step % every == 0; };
+  // A local re-sort (the arrays hold the layout of the handle's last sort) may leave the
+  // values where they are and only write the permutation, which the step reads its parcels
+  // through, writing them to the other buffer (the handle's copy, or the caller's arrays if
+  // the values are in the copy); a step without a sort updates the values where they are,
+  // and the copy's values go back to the caller's arrays once, after the last step. Taken
+  // where no identity array travels with the parcels and no gas iteration reads them before
+  // the step. A re-sort at the call's start then follows the call's volume deposit, which
+  // reads the arrays in the last sort's layout (its integer sums do not depend on the order).
+  const bool perm_sort = !ck && !pc->pid && h->cfg.coupling_iters == 0;
+  bool start_perm = false;
   if (!h->order_on_caller || h->order_np != np || sort_due(h->step_counter)) {
-    // the caller's arrays still hold the last step's layout: re-sort locally
     const bool local = h->order_on_caller && h->order_np == np;
-    mppic_status s = sort_into_scratch<T>(h, pc, dst, false, local, gas);
-    if (s) return s;
-    src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
+    if (local && perm_sort && nsteps > 0) {
+      start_perm = true;
+    } else {
+      mppic_status s = sort_into_scratch<T>(h, pc, dst, false, local, gas);
+      if (s) return s;
+      src = sorted_arrays<T>(h, pc->pid != nullptr, ck);
+    }
   }
   KParams<T> p = make_params<T>(h, gas);
   const KParams<T>* beds = nullptr;
@@ -700,19 +714,16 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   if (s) return s;
   s = launch_cells<T>(h, MODE_VOLUME, p, src, src, nullptr, pc->np, beds);   // Vs of the current positions
   if (s) return s;
+  if (start_perm) {
+    s = sort_into_scratch<T>(h, pc, caller, false, true, gas, true);
+    if (s) return s;
+    src.perm = h->lperm;
+  }
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
-  // A re-sort inside the call may leave the values where they are and only write the
-  // permutation, which the step reads its parcels through, writing them to the other buffer
-  // (the handle's copy, or the caller's arrays if the values are in the copy); a step without
-  // a sort updates the values where they are, and the copy's values go back to the caller's
-  // arrays once, after the last step. Taken where no identity array travels with the parcels
-  // and no gas iteration reads them before the step.
-  const bool perm_sort = !ck && !pc->pid && h->cfg.coupling_iters == 0;
-  const PArrays<T> caller = dst;
   const PArrays<T> copy = sorted_arrays<T>(h, false, false);
-  bool in_copy = false;                          // the current values are in the handle's copy
+  bool in_copy = start_perm;                     // the values are (step 0: go) in the handle's copy
   for (int it = 0; it < nsteps; ++it) {
-    if (it > 0) dst = in_copy ? copy : caller;   // (step 0 writes the caller's arrays)
+    dst = in_copy ? copy : caller;
     if (it > 0 && sort_due(h->step_counter + it)) {
       if (perm_sort) {
         s = sort_into_scratch<T>(h, pc, src, true, true, gas, true);   // keys from the previous step
