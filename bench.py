@@ -641,7 +641,7 @@ def batched_leg(args, steps, with_cpu=True):
     batch = mppic.Batch([b.params for b in beds], [b.np for b in beds], precision=args.precision,
                         sort_every=args.sort_every, stream=stream)
     parcels, gas = mppic.concat_beds(beds, args.precision)
-    tuned = tune.autotune(batch, parcels, gas, steps=10, grids=(0, 1, 2), sorts=(1, 2, 5, 10, 20))
+    tuned = tune.autotune(batch, parcels, gas, steps=10, grids=(0, 2, 3), sorts=(1, 2, 5, 10, 20))
     period = tuned["best"][1]
     rounds = max(1, steps // period)
     steps = rounds * period

@@ -57,7 +57,7 @@ struct mppic_handle {
   u64* acc = nullptr;        // [NQ][words][nnode]
   void* fld = nullptr;       // 5 x nnode T
   int* cstart = nullptr;     // nkeys + 1
-  uint8_t* cellmap = nullptr;  // nbricks * 256: cells ranked by parcel count per brick
+  uint8_t* cellmap = nullptr;  // nbricks * 256: per brick, the upper-half cell of each cell-kernel thread (first CT entries)
   u64* bacc = nullptr;         // [nbricks][NQ][words][TNODES]: bricks' tile slots
   int* bstamp = nullptr;       // [nbricks]: deposit epoch of each slot
   int* epoch = nullptr;        // the current deposit epoch (device counter)
@@ -524,27 +524,32 @@ mppic_status clear_volume_accumulator(mppic_handle* h) {
   return MPPIC_OK;
 }
 
-// One cell kernel instance: its shared-memory attribute and resident CTAs are set up once.
+// One cell kernel instance: its shared-memory attribute (the larger layout, with the grad p
+// planes) and its resident CTAs for each tile layout are set up once.
 template <class T, int MODE, int DRAG, bool BATCH, bool PERM>
-mppic_status cell_kernel_setup(mppic_handle* h, int* resident) {
+mppic_status cell_kernel_setup(mppic_handle* h, bool gp, int* resident) {
   static bool done = false;
-  static int res = 0;
+  static int res[2] = {0, 0};
   if (!done) {
-    const size_t sm = CellSmem<T>::bytes;
     CU(cudaFuncSetAttribute(k_cells<T, MODE, DRAG, BATCH, PERM>,
-                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, k_cells<T, MODE, DRAG, BATCH, PERM>, BCELLS, sm));
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CellSmem<T>::bytes(true)));
+    for (int g = 0; g < 2; ++g)
+      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res[g], k_cells<T, MODE, DRAG, BATCH, PERM>, CT,
+                                                       CellSmem<T>::bytes(g != 0)));
     done = true;
   }
-  *resident = res;
+  *resident = res[gp ? 1 : 0];
   return MPPIC_OK;
 }
 
 template <class T, int MODE, int DRAG, bool BATCH, bool PERM>
 mppic_status launch_cells_b(mppic_handle* h, const KParams<T>& p, PArrays<T> src, PArrays<T> dst,
                             int* cell_out, long long np, const KParams<T>* beds, uint32_t* key_out) {
+  // the node-field tile holds the grad p planes when the gas gives a node field (the same
+  // for every bed of a batch)
+  const bool gp = p.has_gp != 0;
   int resident = 0;
-  mppic_status s = cell_kernel_setup<T, MODE, DRAG, BATCH, PERM>(h, &resident);
+  mppic_status s = cell_kernel_setup<T, MODE, DRAG, BATCH, PERM>(h, gp, &resident);
   if (s) return s;
   if (h->nbricks == 0) return MPPIC_OK;
   // persistent grid: the CTAs that fit on the GPU at once (or grid_factor per SM)
@@ -554,8 +559,9 @@ mppic_status launch_cells_b(mppic_handle* h, const KParams<T>& p, PArrays<T> src
   CU(cudaMemsetAsync(h->wq, 0, sizeof(unsigned long long), h->stream));
   Phase ph(h, MODE == MODE_VOLUME ? PH_DEPOSIT : MODE == MODE_STEP ? PH_STEP : PH_COUPLE);
   ph.launched();
-  k_cells<T, MODE, DRAG, BATCH, PERM><<<(unsigned)grid, BCELLS, CellSmem<T>::bytes, h->stream>>>(
-      p, beds, h->d_brick_bed, h->nbricks, h->wq, src, dst, cell_out, key_out, h->obj_part, np);
+  k_cells<T, MODE, DRAG, BATCH, PERM><<<(unsigned)grid, CT, CellSmem<T>::bytes(gp), h->stream>>>(
+      p, beds, h->d_brick_bed, h->nbricks, h->wq, src, dst, cell_out, key_out, h->obj_part, np,
+      gp ? 1 : 0);
   LAUNCHED();
   return MPPIC_OK;
 }
@@ -1160,9 +1166,9 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
     // no tile slot is valid yet: stamps -1, epoch 0
     if (e == cudaSuccess) e = cudaMemsetAsync(h->bstamp, 0xff, sizeof(int) * (nbricks > 0 ? nbricks : 1), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->epoch, 0, sizeof(int), h->stream);
-    if (e == cudaSuccess) {                      // identity cell map until the first sort
+    if (e == cudaSuccess) {                      // the natural pair map until the first sort
       std::vector<uint8_t> id((size_t)BCELLS * (nbricks > 0 ? nbricks : 1));
-      for (size_t i = 0; i < id.size(); ++i) id[i] = (uint8_t)(i % BCELLS);
+      for (size_t i = 0; i < id.size(); ++i) id[i] = (uint8_t)(i % BCELLS < CT ? i % BCELLS + CT : 0);
       e = cudaMemcpy(h->cellmap, id.data(), id.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess && nbricks > 0) {       // brick geometry for the local re-sort

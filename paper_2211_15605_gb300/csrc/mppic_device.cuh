@@ -404,7 +404,7 @@ struct PArrays {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-constexpr size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ constexpr size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 __device__ __forceinline__ float fpow(float a, float b) { return __powf(a, b); }
 __device__ __forceinline__ double fpow(double a, double b) { return pow(a, b); }
@@ -433,37 +433,38 @@ __device__ __forceinline__ T wen_yu_fast(const KParams<T>& p, T d, T es, const T
 // doubles), node-major planes so the 8 lanes of a quarter-warp (8 consecutive nodes along
 // x) read 128 contiguous bytes:
 //   [0, 4 TNODES)        eps_s, u_g[3] as 4/VW planes of VW-vectors;
-//   [4 TNODES, 8 TNODES) grad p[3] (and a pad) the same way, filled only for a node field;
-//   [8 TNODES, 9 TNODES) tau, one value per node.
+//   with grad p (a node field): [4 TNODES, 8 TNODES) grad p[3] (and a pad) the same way,
+//   then tau at [8 TNODES, 9 TNODES); without: tau at [4 TNODES, 5 TNODES).
 template <class T> struct TileVec;
 template <> struct TileVec<float> { static constexpr int n = 4; };
 template <> struct TileVec<double> { static constexpr int n = 2; };
-constexpr int TILE_VALS = 9;                     // T values per node in the tile
+__host__ __device__ constexpr int tile_vals(bool gp) { return gp ? 9 : 5; }  // T values per node
+__host__ __device__ constexpr int tau_off(bool gp) { return gp ? 8 * TNODES : 4 * TNODES; }
 
-// Offset (in T) of field f of tile node tn.
+// Offset (in T) of field f of tile node tn (ta = tau_off of the tile's layout).
 template <class T>
-__device__ __forceinline__ int tile_off(int f, int tn) {
+__device__ __forceinline__ int tile_off(int f, int tn, int ta) {
   constexpr int VW = TileVec<T>::n;
   if (f < 4) return VW * ((f / VW) * TNODES + tn) + f % VW;
-  if (f == 4) return 8 * TNODES + tn;
+  if (f == 4) return ta + tn;
   const int g = f - 5;
   return 4 * TNODES + VW * ((g / VW) * TNODES + tn) + g % VW;
 }
 
-__device__ __forceinline__ void tile_node(const float* t, int n, bool gpf, float (&v)[8]) {
+__device__ __forceinline__ void tile_node(const float* t, int n, bool gpf, int ta, float (&v)[8]) {
   const float4 a = *reinterpret_cast<const float4*>(t + 4 * n);
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  v[4] = t[8 * TNODES + n];
+  v[4] = t[ta + n];
   if (gpf) {
     const float4 g = *reinterpret_cast<const float4*>(t + 4 * (TNODES + n));
     v[5] = g.x; v[6] = g.y; v[7] = g.z;
   }
 }
-__device__ __forceinline__ void tile_node(const double* t, int n, bool gpf, double (&v)[8]) {
+__device__ __forceinline__ void tile_node(const double* t, int n, bool gpf, int ta, double (&v)[8]) {
   const double2 a0 = *reinterpret_cast<const double2*>(t + 2 * n);
   const double2 a1 = *reinterpret_cast<const double2*>(t + 2 * (TNODES + n));
   v[0] = a0.x; v[1] = a0.y; v[2] = a1.x; v[3] = a1.y;
-  v[4] = t[8 * TNODES + n];
+  v[4] = t[ta + n];
   if (gpf) {
     const double2 g0 = *reinterpret_cast<const double2*>(t + 2 * (2 * TNODES + n));
     const double2 g1 = *reinterpret_cast<const double2*>(t + 2 * (3 * TNODES + n));
@@ -473,18 +474,30 @@ __device__ __forceinline__ void tile_node(const double* t, int n, bool gpf, doub
 
 // ------------------------------------------------------------ cell kernel --
 
-// Shared memory of the cell kernels (sections 128-byte aligned).
-constexpr int PSTAGES = 5;                       // parcel levels in flight per thread
+// Threads of a cell-kernel CTA: thread t owns two cells of its brick, local cell t of the
+// lower half and the cell of the upper half the brick's pair map gives it (set at each sort,
+// pair_layout in mppic_sort.cuh), and walks the parcels of the first, then of the second.
+constexpr int CT = BCELLS / 2;
+
+// Shared memory of the cell kernels (sections 128-byte aligned), for a node-field tile with
+// or without the grad p planes (gp):
+//   fld  node-field tile (tile_vals(gp) values per node); after the parcel loop it holds the
+//        objective partials [3][CT];
+//   fx   [NQ][W][TNODES] u64: exact fixed-point sums (parcels off their sorted cell; in the
+//        FP32 form also the exact volume of the cells' own parcels);
+//   tile [NQ][TNODES] T: the node sums of the cells' own parcels (after the parcel loop);
+//   cbuf [NQ*8][CT] T and [CT] long long: the 40 corner sums (and exact volume) a thread's
+//        first cell leaves when the thread moves on to its second.
 template <class T>
 struct CellSmem {
   static constexpr int W = Words<T>::n;
-  static constexpr size_t fld = 0;                                         // node-field tile
-  static constexpr size_t fx = rup(fld + sizeof(T) * TILE_VALS * TNODES, 128);  // [NQ][W][TNODES] u64
-  static constexpr size_t tile = rup(fx + sizeof(u64) * NQ * W * TNODES, 128);  // [NQ][TNODES] T
-  static constexpr size_t red = rup(tile + sizeof(T) * NQ * TNODES, 128);  // [3][BCELLS] T
-  static constexpr size_t pre = rup(red + sizeof(T) * 3 * BCELLS, 128);    // [PSTAGES][8][BCELLS] T
-  static constexpr size_t bytes = pre + sizeof(T) * PSTAGES * 8 * BCELLS;
+  __host__ __device__ static constexpr size_t fx(bool gp) { return rup(sizeof(T) * tile_vals(gp) * TNODES, 128); }
+  __host__ __device__ static constexpr size_t tile(bool gp) { return rup(fx(gp) + sizeof(u64) * NQ * W * TNODES, 128); }
+  __host__ __device__ static constexpr size_t cbuf(bool gp) { return rup(tile(gp) + sizeof(T) * NQ * TNODES, 128); }
+  __host__ __device__ static constexpr size_t vbuf(bool gp) { return cbuf(gp) + sizeof(T) * NQ * 8 * CT; }
+  __host__ __device__ static constexpr size_t bytes(bool gp) { return vbuf(gp) + sizeof(long long) * CT; }
 };
+static_assert(sizeof(float) * 3 * CT <= sizeof(float) * 5 * TNODES, "objective partials fit the tile");
 
 // Asynchronous copy of one parcel value into this thread's prefetch slot.
 __device__ __forceinline__ void cp_async(float* dst, const float* src) {
@@ -646,6 +659,15 @@ template <> struct CellSums<double> {
     }
   }
   __device__ __forceinline__ double get(int q, int k) const { return v[q][k]; }
+  // quantities [Q0, Q1) into cb ([NQ*4][CT] double2, see cbuf_get) as thread t's
+  template <int Q0, int Q1>
+  __device__ __forceinline__ void store(double* cb, int t) const {
+    double2* c2 = reinterpret_cast<double2*>(cb);
+#pragma unroll
+    for (int q = Q0; q < Q1; ++q)
+#pragma unroll
+      for (int h = 0; h < 4; ++h) c2[(q * 4 + h) * CT + t] = make_double2(v[q][2 * h], v[q][2 * h + 1]);
+  }
 };
 template <> struct CellSums<float> {
   float2 v[NQ][4];
@@ -675,14 +697,32 @@ template <> struct CellSums<float> {
   __device__ __forceinline__ float get(int q, int k) const {
     return (k & 1) ? v[q][k >> 1].y : v[q][k >> 1].x;
   }
+  // quantities [Q0, Q1) into cb ([NQ*2][CT] float4, see cbuf_get) as thread t's
+  template <int Q0, int Q1>
+  __device__ __forceinline__ void store(float* cb, int t) const {
+    float4* c4 = reinterpret_cast<float4*>(cb);
+#pragma unroll
+    for (int q = Q0; q < Q1; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        c4[(q * 2 + h) * CT + t] = make_float4(v[q][2 * h].x, v[q][2 * h].y, v[q][2 * h + 1].x, v[q][2 * h + 1].y);
+  }
 };
+
+// Corner k of quantity q of the sums thread t left in cb (CellSums::store): vectors of VW
+// corners, [NQ * 8 / VW][CT], so that the threads of a warp store and load contiguous vectors.
+template <class T>
+__device__ __forceinline__ T cbuf_get(const T* cb, int q, int k, int t) {
+  constexpr int VW = TileVec<T>::n;
+  return cb[((q * (8 / VW) + k / VW) * CT + t) * VW + k % VW];
+}
 
 // Interpolation at one parcel from the brick's node-field tile (corner (0,0,0) at tile node
 // base) with precomputed weights. The gradient of the trilinear interpolant of tau is
 // formed from differences across the cell faces: d/dx = (1/dx) sum_{b,c} (tau_1bc -
 // tau_0bc) w_y,b w_z,c, and likewise for y and z.
 template <class T>
-__device__ __forceinline__ void interp_tile_w(const KParams<T>& p, const T* t, int base,
+__device__ __forceinline__ void interp_tile_w(const KParams<T>& p, const T* t, int base, int ta,
                                               const Weights<T>& w, Interp<T>& r) {
   T tau[8];
   r.es = 0;
@@ -691,7 +731,7 @@ __device__ __forceinline__ void interp_tile_w(const KParams<T>& p, const T* t, i
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     T v[8];
-    tile_node(t, base + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2)), gpf, v);
+    tile_node(t, base + (q & 1) + TX * (((q >> 1) & 1) + TY * (q >> 2)), gpf, ta, v);
     const T Wq = w.W.get(q);
     r.es += Wq * v[0];
     r.ug[0] += Wq * v[1];
@@ -725,7 +765,7 @@ __device__ __forceinline__ void interp_tile_w(const KParams<T>& p, const T* t, i
 // (u_g,y, u_g,z) are summed as two pairs per corner, and the x and y components of the
 // stress gradient as one pair (each lane one rounded operation: the scalar values).
 __device__ __forceinline__ void interp_tile_w(const KParams<float>& p, const float* t, int base,
-                                              const Weights<float>& w, Interp<float>& r) {
+                                              int ta, const Weights<float>& w, Interp<float>& r) {
   float2 e0 = make_float2(0.0f, 0.0f), e1 = make_float2(0.0f, 0.0f), g01 = make_float2(0.0f, 0.0f);
   float g2 = 0.0f;
   float tau[8];
@@ -738,7 +778,7 @@ __device__ __forceinline__ void interp_tile_w(const KParams<float>& p, const flo
     const float2 W2 = make_float2(Wq, Wq);
     e0 = __ffma2_rn(W2, make_float2(a.x, a.y), e0);
     e1 = __ffma2_rn(W2, make_float2(a.z, a.w), e1);
-    tau[q] = t[8 * TNODES + n];
+    tau[q] = t[ta + n];
     if (gpf) {
       const float4 g = *reinterpret_cast<const float4*>(t + 4 * (TNODES + n));
       g01 = __ffma2_rn(W2, make_float2(g.x, g.y), g01);
@@ -859,9 +899,9 @@ __device__ __forceinline__ T drag_step(const KParams<T>& p, T d, T es, const T (
   }
 }
 
-// Deterministic sum of three per-thread values over the CTA: a fixed shuffle tree in
-// each warp, then the warp partials in warp order.
-template <class T>
+// Deterministic sum of three per-thread values over the CTA (NW warps): a fixed shuffle tree
+// in each warp, then the warp partials in warp order.
+template <int NW, class T>
 __device__ void cta_sum3(T a, T b, T c, T* sm, double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -874,16 +914,18 @@ __device__ void cta_sum3(T a, T b, T c, T* sm, double* out) {
   __syncthreads();
   if (threadIdx.x == 0) {
     T A = 0, B = 0, C = 0;
-    for (int w = 0; w < BCELLS / 32; ++w) { A += sm[3 * w]; B += sm[3 * w + 1]; C += sm[3 * w + 2]; }
+    for (int w = 0; w < NW; ++w) { A += sm[3 * w]; B += sm[3 * w + 1]; C += sm[3 * w + 2]; }
     out[0] = (double)A; out[1] = (double)B; out[2] = (double)C;
   }
 }
 
-// The cell kernel. One CTA owns one brick (taken from a work counter: persistent grid);
-// thread t owns the cell cellmap gives it (its own cell, or the cell of count rank t),
-// warp w the group of threads 32w..32w+31, whose parcels are stored by level
-// (level_layout, at each sort). The warp's r-th iteration processes the r-th parcel of
-// each of its cells that has one, one per thread, with coalesced loads and stores.
+// The cell kernel. One CTA of CT threads owns one brick (taken from a work counter:
+// persistent grid). Thread t owns two cells of it: local cell t of the lower half and the
+// upper-half cell of the brick's pair map (chosen at each sort so that the threads' parcel
+// counts are even, pair_layout); it walks the parcels of the first cell, then those of the
+// second. Warp w (threads 32w..32w+31) stores its threads' parcels by level (the r-th parcel
+// of every thread that has one, in thread order), so the warp's r-th iteration reads and
+// writes one contiguous run.
 // MODE_VOLUME: deposit the solids volume of the current positions.
 // MODE_STEP: one full step (interp from a shared node-field tile, drag, drag sums,
 // objectives, push, walls, re-bin), depositing the solids volume of the new positions
@@ -892,31 +934,34 @@ __device__ void cta_sum3(T a, T b, T c, T* sm, double* out) {
 // before a sort, so the sort needs no key pass).
 // MODE_DRAG: the drag sums A, B of the current state against the current node gas velocity,
 // parcels unchanged (a gas iteration of implicit coupling).
-// A thread sums the contributions of its own cell's parcels (old position for the drag
-// sums, new position for the volume) at the cell's 8 corners in registers: up to 40 sums,
-// added once per brick to a shared node tile in 8 corner phases (no two cells of a phase
-// share a node). In the FP32 form the thread also sums its parcels' volumes exactly in
-// fixed point, and the corner with the largest sum takes that total minus the other seven,
-// so the deposited volume of a cell is exactly the sum of its parcels' volumes. A parcel
-// that is not in its sorted cell (it drifted since the last sort, or moved this step) adds
-// its contributions in exact fixed point to a second shared tile (or, outside the brick,
-// to the global accumulators). Both tiles go to the brick's slot in fixed point once per
-// brick. Threads wait on each other only at the brick's start and end.
+// A thread sums the contributions of its current cell's parcels (old position for the drag
+// sums, new position for the volume) at the cell's 8 corners in registers: up to 40 sums.
+// When it moves on to its second cell it leaves the first cell's sums in shared memory;
+// at the brick's end both cells' sums are added to a shared node tile in 8 corner phases
+// (no two cells of a phase share a node, so plain adds in a fixed order are deterministic).
+// In the FP32 form the thread also sums its parcels' volumes exactly in fixed point, per
+// cell, and the corner with the largest sum takes that total minus the other seven, so the
+// deposited volume of a cell is exactly the sum of its parcels' volumes. A parcel that is not
+// in its sorted cell (it drifted since the last sort, or moved this step) adds its
+// contributions in exact fixed point to a second shared tile (or, outside the brick, to the
+// global accumulators). Both tiles go to the brick's slot in fixed point once per brick.
+// Threads wait on each other only at the brick's start and end.
 // DRAG: 0 Wen-Yu only, 1 the drag closure of each bed's drag_model.
+// gp_tile: the node-field tile holds the grad p planes (some bed has a node field).
 template <class T> struct CellOccupancy;
-template <> struct CellOccupancy<float> { static constexpr int ctas = 2; };
-template <> struct CellOccupancy<double> { static constexpr int ctas = 1; };
+template <> struct CellOccupancy<float> { static constexpr int ctas = 3; };
+template <> struct CellOccupancy<double> { static constexpr int ctas = 2; };
 
 // BATCH: the parameters of each brick's bed come from `beds` (copied to shared memory when
 // the bed changes); otherwise from p0, which the kernel reads in place from its constant
 // parameter space (no copy, no per-use shared-memory load).
 template <class T, int MODE, int DRAG, bool BATCH, bool PERM = false>
-__global__ void __launch_bounds__(BCELLS, CellOccupancy<T>::ctas)
+__global__ void __launch_bounds__(CT, CellOccupancy<T>::ctas)
 k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ beds,
         const int* __restrict__ brick_bed, long long total_bricks,
         unsigned long long* __restrict__ work, PArrays<T> src, PArrays<T> dst,
         int* __restrict__ cell_out, uint32_t* __restrict__ key_out, double* __restrict__ obj_part,
-        long long np) {
+        long long np, int gp_tile) {
   typedef CellSmem<T> S;
   constexpr int W = S::W;
   constexpr bool EXACT_V = W == 1 && MODE != MODE_DRAG;  // FP32 form: exact cell volume totals
@@ -924,13 +969,16 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   __shared__ KParams<T> sp;                        // parameters of the current brick's bed
   __shared__ long long s_brick;
   __shared__ int s_kr[2];                          // node layers deposited into by this brick
-  T* sf = reinterpret_cast<T*>(smem + S::fld);     // node-field tile (planes)
-  T* pre = reinterpret_cast<T*>(smem + S::pre);    // [PSTAGES][8][BCELLS] prefetched parcels
-  u64* fx = reinterpret_cast<u64*>(smem + S::fx);  // [NQ][W][TNODES] parcels off their sorted cell
-  T* tile = reinterpret_cast<T*>(smem + S::tile);  // [NQ][TNODES] sums of the cells' own parcels
-  T* red = reinterpret_cast<T*>(smem + S::red);
+  __shared__ int s_wsum[CT / 32];                  // parcels of each warp's cells
+  const bool gpl = gp_tile != 0;
+  const int ta = tau_off(gpl);                     // tau plane of the node-field tile
+  T* sf = reinterpret_cast<T*>(smem);              // node-field tile (planes)
+  u64* fx = reinterpret_cast<u64*>(smem + S::fx(gpl));  // [NQ][W][TNODES] exact fixed point
+  T* tile = reinterpret_cast<T*>(smem + S::tile(gpl));  // [NQ][TNODES] sums of the cells' own parcels
+  T* cbuf = reinterpret_cast<T*>(smem + S::cbuf(gpl));  // sums of each thread's first cell
+  long long* vbuf = reinterpret_cast<long long*>(smem + S::vbuf(gpl));
+  T* red = sf;                                     // after the parcel loop: objective partials
 
-  __shared__ int s_wsum[BCELLS / 32];             // parcels of each warp's cells
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const unsigned below = (1u << lane) - 1u;
@@ -954,30 +1002,29 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
     return;
   }
 
-  // this thread's cell (from the cell map of the last sort) and its parcels
-  const int lc = p.cellmap[kbase + tid];
-  const int lti = lc % BX, ltj = (lc / BX) % BY, ltk = lc / (BX * BY);
-  const int tn0 = lti + TX * (ltj + TY * ltk);   // tile node of this cell's corner (0,0,0)
-  const int n = p.cstart[kbase + lc + 1] - p.cstart[kbase + lc];
+  // this thread's cells (the second from the pair map of the last sort) and their parcels
+  const int lcB = p.cellmap[kbase + tid];
+  const int nA = p.cstart[kbase + tid + 1] - p.cstart[kbase + tid];
+  const int nB = p.cstart[kbase + lcB + 1] - p.cstart[kbase + lcB];
+  const int n = nA + nB;
   {
     const int ws = __reduce_add_sync(FULL, n);
     if (lane == 0) s_wsum[warp] = ws;
   }
-  for (int e = tid + q0 * W * TNODES; e < q1 * W * TNODES; e += BCELLS) fx[e] = 0;
-  for (int e = tid + q0 * TNODES; e < q1 * TNODES; e += BCELLS) tile[e] = 0;
+  for (int e = tid + q0 * W * TNODES; e < q1 * W * TNODES; e += CT) fx[e] = 0;
   if (tid == 0) { s_kr[0] = 1 << 30; s_kr[1] = -1; }
   if (MODE != MODE_VOLUME) {
     // asynchronous copies, all in flight at once; absent nodes and fields are zero. The drag
     // sums need only eps_s and u_g.
     constexpr int nf = MODE == MODE_DRAG ? 4 : 8;
-    for (int tn = tid; tn < TNODES; tn += BCELLS) {
+    for (int tn = tid; tn < TNODES; tn += CT) {
       const int i = bi0 + tn % TX, j = bj0 + (tn / TX) % TY, k = bk0 + tn / (TX * TY);
       const bool in = i <= p.nx && j <= p.ny && k <= p.nz;
       const long long nid = in ? node_id(p, i, j, k) : 0;
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
         if (f >= 5 && !p.has_gp) continue;       // grad p planes are read only for a node field
-        T* dstv = sf + tile_off<T>(f, tn);
+        T* dstv = sf + tile_off<T>(f, tn, ta);
         if (in)
           cp_async(dstv, (f < 5 ? (const T*)p.fld[f] : p.gpf[f - 5]) + nid);
         else
@@ -989,72 +1036,63 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   }
   __syncthreads();
 
-  const int ci = bi0 + lti, cj = bj0 + ltj, ck = bk0 + ltk;    // this thread's cell
+  // the cell whose parcels the thread walks (the first one with parcels), and sw: the level
+  // at which it moves on to the second (-1: it does not)
+  int lc = nA > 0 ? tid : lcB;
+  const int sw = nA > 0 && nB > 0 ? nA : -1;
+  int ci = bi0 + lc % BX, cj = bj0 + (lc / BX) % BY, ck = bk0 + lc / (BX * BY);
   const int nmax = __reduce_max_sync(FULL, n);
   int off = p.cstart[kbase];                     // the group's first parcel
   for (int w = 0; w < warp; ++w) off += s_wsum[w];
   CellSums<T> sums;
   sums.zero();
-  long long vtot = 0;                            // EXACT_V: this cell's volume, fixed point
+  long long vtot = 0;                            // EXACT_V: the current cell's volume, fixed point
   T o_dp = 0, o_hn = 0, o_vs = 0;
 
-  // Level r's parcel values are copied into this thread's slots of stage r % PSTAGES
-  // PSTAGES-1 levels ahead of their use; each thread reads only its own slots, so it waits
-  // only for its own copies. Every iteration commits one group (possibly empty).
-  // PERM (the step after a sort that wrote only the permutation): the values of layout
-  // position q are read from index src.perm[q]; each prefetch loads the next level's index,
-  // so that its latency is covered by one iteration.
-  int pf_off = off;                              // first position of the next level to prefetch
+  // Level r+1's parcel values are loaded into registers (nv) while level r is processed, so
+  // that their latency is covered by one iteration. PERM (the step after a sort that wrote
+  // only the permutation): the values of layout position q are read from index src.perm[q];
+  // each level's load also fetches the next level's index, one iteration ahead of its use.
+  int pf_off = off;                              // first position of the next level to load
   uint32_t pf_src = 0;                           // PERM: this thread's index in that level
   auto perm_at = [&](int lv, int base) -> uint32_t {
     const bool a = n > lv;
     const unsigned bl = __ballot_sync(FULL, a);
     return a ? __ldg(src.perm + base + __popc(bl & below)) : 0u;
   };
-  auto prefetch = [&](int lv, bool next) {
+  T nv[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) nv[f] = T(0);
+  auto load_level = [&](int lv) {
     const bool a = n > lv;
     const unsigned bl = __ballot_sync(FULL, a);
     if (a) {
       const int q = pf_off + __popc(bl & below);
       const uint32_t sq = PERM ? pf_src : (uint32_t)q;
-      T* slot = pre + (lv % PSTAGES) * 8 * BCELLS + tid;
 #pragma unroll
       for (int f = 0; f < 8; ++f)
-        if (MODE != MODE_VOLUME || f < 3 || f >= 6) cp_async(slot + f * BCELLS, src.a[f] + sq);
+        if (MODE != MODE_VOLUME || f < 3 || f >= 6) nv[f] = src.a[f][sq];
     }
     pf_off += __popc(bl);
-    if (PERM && next && lv + 1 < nmax) pf_src = perm_at(lv + 1, pf_off);
+    if (PERM && lv + 1 < nmax) pf_src = perm_at(lv + 1, pf_off);
   };
-  if (PERM) {                    // the first PSTAGES levels' indices, all loads in flight at once
-    uint32_t pv[PSTAGES];
-    int base = pf_off;
-#pragma unroll
-    for (int lv = 0; lv < PSTAGES; ++lv) {
-      const bool a = n > lv;
-      const unsigned bl = __ballot_sync(FULL, a);
-      pv[lv] = a ? __ldg(src.perm + base + __popc(bl & below)) : 0u;
-      base += __popc(bl);
-    }
-#pragma unroll
-    for (int lv = 0; lv < PSTAGES - 1; ++lv) {
-      pf_src = pv[lv];
-      if (lv < nmax) prefetch(lv, false);
-      cp_async_commit();
-    }
-    pf_src = pv[PSTAGES - 1];
-  } else {
-#pragma unroll
-    for (int lv = 0; lv < PSTAGES - 1; ++lv) {
-      if (lv < nmax) prefetch(lv, false);
-      cp_async_commit();
-    }
-  }
+  if (PERM && nmax > 0) pf_src = perm_at(0, pf_off);
+  if (nmax > 0) load_level(0);
   for (int r = 0; r < nmax; ++r) {
-    if (r + PSTAGES - 1 < nmax) prefetch(r + PSTAGES - 1, true);
-    cp_async_commit();
-    cp_async_wait<PSTAGES - 1>();
+    T cv[8];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) cv[f] = nv[f];
+    if (r + 1 < nmax) load_level(r + 1);
     const bool act = n > r;
     const unsigned bal = __ballot_sync(FULL, act);
+    if (r == sw) {               // the first cell is done: leave its sums, go on to the second
+      sums.template store<q0, q1>(cbuf, tid);
+      if (EXACT_V) vbuf[tid] = vtot;
+      sums.zero();
+      vtot = 0;
+      lc = lcB;
+      ci = bi0 + lc % BX; cj = bj0 + (lc / BX) % BY; ck = bk0 + lc / (BX * BY);
+    }
     // parcels off their sorted cell: recorded here, deposited by the whole warp below
     bool off_old = false, off_new = false;       // at the old position / the new one
     int co = 0, cno = 0;                         // their cell ids
@@ -1062,9 +1100,8 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
     T V = T(0), fd[4] = {T(0), T(0), T(0), T(0)};
     if (act) {
       const int q = off + __popc(bal & below);
-      const T* slot = pre + (r % PSTAGES) * 8 * BCELLS + tid;
-      const T x = slot[0], y = slot[BCELLS], z = slot[2 * BCELLS];
-      const T d = slot[6 * BCELLS], om = slot[7 * BCELLS];
+      const T x = cv[0], y = cv[1], z = cv[2];
+      const T d = cv[6], om = cv[7];
       Cell3<T> c;
       const bool own = bin3_expect(p, x, y, z, ci, cj, ck, c);
       V = om * (d * d * d) * p.vcoef;
@@ -1083,14 +1120,14 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
           off_old = true;
         }
       } else {
-        const T u = slot[3 * BCELLS], v = slot[4 * BCELLS], w = slot[5 * BCELLS];
+        const T u = cv[3], v = cv[4], w = cv[5];
         const int ti = c.i - bi0, tj = c.j - bj0, tk = c.k - bk0;
         const bool inb = ti >= 0 && ti < BX && tj >= 0 && tj < BY && tk >= 0 && tk < BZ;
         Weights<T> wt;
         all_weights(c.xi, wt);
         Interp<T> I;
         if (inb) {
-          interp_tile_w(p, sf, ti + TX * (tj + TY * tk), wt, I);
+          interp_tile_w(p, sf, ti + TX * (tj + TY * tk), ta, wt, I);
         } else {  // outside the brick (rare): from the global node arrays
           Fields<T> FG;
           for (int f = 0; f < 5; ++f) FG.f[f] = p.fld[f];
@@ -1178,18 +1215,24 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   }
   // ---- node layers of this brick's own-cell deposits (off-cell deposits recorded theirs
   // as they were made); merged into the global range below, for the next finalize
+  const int ckA = bk0 + tid / (BX * BY), ckB = bk0 + lcB / (BX * BY);
   {
-    const int klo = __reduce_min_sync(FULL, n > 0 ? ck : (1 << 30));
-    const int khi = __reduce_max_sync(FULL, n > 0 ? ck + 1 : -1);
+    const int lo = nA > 0 ? ckA : (nB > 0 ? ckB : (1 << 30));
+    const int hi = nB > 0 ? ckB + 1 : (nA > 0 ? ckA + 1 : -1);
+    const int klo = __reduce_min_sync(FULL, lo);
+    const int khi = __reduce_max_sync(FULL, hi);
     if (lane == 0 && khi >= 0) { atomicMin(&s_kr[0], klo); atomicMax(&s_kr[1], khi); }
   }
-  // ---- FP32 volume: the 8 corner sums in fixed point, the largest replaced by the cell's
-  // exact total minus the other seven
-  long long vfx[8];
+  // the cell whose sums are in registers (lc, if the thread has parcels), the one left in
+  // cbuf (the first, if the thread moved on)
+  const bool has_reg = n > 0, has_buf = sw >= 0;
+  // ---- FP32 volume: the 8 corner sums of each cell in fixed point, the largest replaced by
+  // the cell's exact total minus the other seven
+  long long vfx[8], vfb[8];
   if (EXACT_V) {
-    long long sum7 = 0;
-    int kmax = 0;
-    T vmax = sums.get(0, 0);
+    long long sum7 = 0, sumb = 0;
+    int kmax = 0, kmb = 0;
+    T vmax = sums.get(0, 0), vmb = has_buf ? cbuf_get(cbuf, 0, 0, tid) : T(0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       u64 f[W];
@@ -1197,25 +1240,42 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
       vfx[k] = (long long)f[0];
       sum7 += vfx[k];
       if (sums.get(0, k) > vmax) { vmax = sums.get(0, k); kmax = k; }
+      const T bv = has_buf ? cbuf_get(cbuf, 0, k, tid) : T(0);
+      to_fixed(bv, p.mV, f, p.errs);
+      vfb[k] = (long long)f[0];
+      sumb += vfb[k];
+      if (bv > vmb) { vmb = bv; kmb = k; }
     }
+    const long long vtb = has_buf ? vbuf[tid] : 0ll;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 8; ++k) {
       if (k == kmax) vfx[k] += vtot - sum7;
+      if (k == kmb) vfb[k] += vtb - sumb;
+    }
   }
-  // ---- this cell's sums into the tiles, one corner per phase: in a phase no two cells touch
+  // ---- the cells' sums into the tiles, one corner per phase: in a phase no two cells touch
   // the same node, so plain adds in a fixed order are deterministic (the off-cell atomics
-  // into fx are complete: the loop is over)
+  // into fx are complete: the loop is over).
+  constexpr int qt = EXACT_V ? 1 : q0;           // first quantity summed in the float tile
+  __syncthreads();
+  for (int e = tid + qt * TNODES; e < q1 * TNODES; e += CT) tile[e] = T(0);
+  const int tnR = lc % BX + TX * ((lc / BX) % BY + TY * (lc / (BX * BY)));
+  const int tnA = tid % BX + TX * ((tid / BX) % BY + TY * (tid / (BX * BY)));
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     __syncthreads();
-    if (n > 0) {
-      const int tn = tn0 + (k & 1) + TX * (((k >> 1) & 1) + TY * (k >> 2));
+    const int ko = (k & 1) + TX * (((k >> 1) & 1) + TY * (k >> 2));
+    if (has_reg) {
+      const int tn = tnR + ko;
       if (EXACT_V) fx[tn] += (u64)vfx[k];
-      else if (MODE != MODE_DRAG) tile[tn] += sums.get(0, k);
-      if (MODE != MODE_VOLUME) {
 #pragma unroll
-        for (int q = 1; q < NQ; ++q) tile[q * TNODES + tn] += sums.get(q, k);
-      }
+      for (int q = qt; q < q1; ++q) tile[q * TNODES + tn] += sums.get(q, k);
+    }
+    if (has_buf) {
+      const int tn = tnA + ko;
+      if (EXACT_V) fx[tn] += (u64)vfb[k];
+#pragma unroll
+      for (int q = qt; q < q1; ++q) tile[q * TNODES + tn] += cbuf_get(cbuf, q, k, tid);
     }
   }
   __syncthreads();
@@ -1225,10 +1285,10 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   // node), stamped with this deposit's epoch
   {
     u64* slot = p.bacc + b * (long long)(NQ * W * TNODES);
-    for (int e = tid + q0 * TNODES; e < q1 * TNODES; e += BCELLS) {
+    for (int e = tid + q0 * TNODES; e < q1 * TNODES; e += CT) {
       const int qq = e / TNODES, tn = e % TNODES;
-      u64 f[W];
-      to_fixed(tile[e], qq == 0 ? p.mV : p.mA, f, p.errs);
+      u64 f[W] = {};
+      if (!(EXACT_V && qq == 0)) to_fixed(tile[e], qq == 0 ? p.mV : p.mA, f, p.errs);
       u64 carry = 0;
 #pragma unroll
       for (int w = 0; w < W; ++w) {
@@ -1242,7 +1302,7 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
     }
     if (tid == 0) p.bstamp[b] = epoch;
   }
-  if (MODE == MODE_STEP) cta_sum3(o_dp, o_hn, o_vs, red, obj_part + 3 * b);
+  if (MODE == MODE_STEP) cta_sum3<CT / 32>(o_dp, o_hn, o_vs, red, obj_part + 3 * b);
   };  // one brick
 
   for (long long iter = 0; iter < total_bricks; ++iter) {

@@ -392,7 +392,7 @@ k_rs_build(PArrays<T> src, PArrays<T> dst, const int* __restrict__ bstart,
   const int bs = bstart[B], n = bcount[B];
   if (n == 0) {                                  // uniform: an empty brick
     cstart[k0 + t] = bs;
-    cellmap[k0 + t] = (uint8_t)t;
+    if (t < CT) cellmap[k0 + t] = (uint8_t)(t + CT);   // the natural pair map
     return;
   }
   uint32_t* is = bsrc + bs;

@@ -278,88 +278,43 @@ __global__ void k_cell_starts(const uint32_t* __restrict__ skey, long long nbric
 // ------------------------------------------------------------ level layout --
 
 
-// The step kernel runs one thread per cell and one warp per group of 32 cells of a brick.
-// A warp iterates as often as its fullest cell holds parcels. Where the brick's cells hold
-// very uneven numbers (a sparse bed, or a brick cut by the domain boundary), the cells are
-// ranked by parcel count (descending, ties by cell index) and warp w takes ranks
-// 32w..32w+31, so a warp's cells hold similar numbers and empty cells share warps that
-// finish at once; otherwise thread t keeps cell t (a warp's cells then form an 8x4 block,
-// whose node-tile reads are conflict-free). The choice is made per brick at each sort:
-// ranking is taken if it saves more than a quarter of the warp iterations (it is not tried
-// where no cell is empty and the largest count is at most 1.5 times the smallest). Within a
-// group the parcels are laid out by level: level r holds the r-th parcel (in sorted order)
-// of every cell of the group that has more than r parcels, in rank order; the warp's r-th
-// iteration then reads one contiguous run.
-// level_layout ranks the cells (rank_cells), records the mapping in
-// cellmap, and permutes the parcel arrays into the layout straight from the sorted order.
-// Both sorts end in it: the full radix sort (k_level_gather) and the local re-sort
-// (k_rs_build, in mppic_resort.cuh).
+// The step kernel runs CT = 128 threads per brick: thread t walks the parcels of two
+// cells, local cell t of the lower half of the brick and one cell of the upper half (the
+// brick's pair map, cellmap[brick * 256 + t]), and a CTA's time follows its largest
+// per-thread parcel count (its warps wait for each other at the brick's end). The natural
+// pairing gives thread t cell t + 128, one half-brick above: the warp's cells then form two
+// 8x4 blocks whose node-tile reads are conflict-free. Where the counts are uneven (a
+// fluidised bed: bubbles and clusters), the lower-half cells ranked by count (descending,
+// ties by cell index) take the upper-half cells ranked the other way (ascending, ties by
+// cell index), so a heavy cell shares its thread with a light one. The choice is made per
+// brick at each sort: the count pairing is taken if it lowers the largest per-thread count
+// by more than a tenth (it is not tried where the natural pairing is already within a tenth
+// of the mean). Within a warp the parcels are laid out by level: level r holds the r-th
+// parcel of each thread's sequence (its first cell's parcels in sorted order, then its
+// second cell's) for every thread whose sequence is longer than r, in thread order; the
+// warp's r-th iteration then reads one contiguous run.
+// level_layout chooses the pairing, records it in cellmap, and permutes the parcel arrays
+// into the layout straight from the sorted order. Both sorts end in it: the full radix sort
+// (k_level_gather) and the local re-sort (k_rs_build, in mppic_resort.cuh). It runs on
+// BCELLS threads: thread t lays out the even levels (t < CT) or the odd levels (t >= CT) of
+// the cell kernel's thread t mod CT.
 struct LevelSmem {
-  union {
-    uint32_t sk[BCELLS];         // bitonic ranking keys
-    int hist[8][BCELLS];         // count ranking: per warp, cells of each count
-  };
-  int gt[BCELLS];                // cells with a larger count
-  uint8_t inv[BCELLS];           // cell of each rank
-  int wa[BCELLS / 32], wb[BCELLS / 32];
-  int rank;
+  uint32_t sk[BCELLS];           // ranking keys: each half sorted on its own
+  uint8_t pb[CT];                // upper-half cell of each thread under the count pairing
+  int wa[BCELLS / 32];
+  int mx[BCELLS / 32];
 };
 
-// Rank of each cell t by (count descending, index ascending) into ls.inv (cell of rank r).
-// Counts below 256: a count histogram (per warp, so ties keep index order); otherwise a
-// bitonic sort of unique (count, index) keys. Both give the same permutation.
-__device__ __forceinline__ void rank_cells(int cnt, int big, LevelSmem& ls) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (!big) {
-    const unsigned below = (1u << lane) - 1u;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) ls.hist[w][t] = 0;
-    __syncthreads();
-    const unsigned m = match_bits<8>((unsigned)cnt);
-    if ((m & below) == 0) ls.hist[warp][cnt] = __popc(m);
-    __syncthreads();
-    // per count c = t: cells in earlier warps (exclusive over warps), and the total
-    int tot = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      const int h = ls.hist[w][t];
-      ls.hist[w][t] = tot;
-      tot += h;
-    }
-    // cells with a count above t: total minus the inclusive scan up to t
-    int inc = tot;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += u;
-    }
-    if (lane == 31) ls.wa[warp] = inc;
-    __syncthreads();
-    int pre = 0, all = 0;
-    for (int w = 0; w < 8; ++w) {
-      if (w < warp) pre += ls.wa[w];
-      all += ls.wa[w];
-    }
-    ls.gt[t] = all - (pre + inc);
-    __syncthreads();
-    const int r = ls.gt[cnt] + ls.hist[warp][cnt] + __popc(m & below);
-    ls.inv[r] = (uint8_t)t;
-    __syncthreads();
-    return;
-  }
-  ls.sk[t] = ((0xFFFFFFu - (uint32_t)min(cnt, 0xFFFFFF)) << 8) | (uint32_t)t;
+// Largest v over the CTA (BCELLS threads); ls.mx is reused, so callers sync between uses.
+__device__ __forceinline__ int cta_max(int v, LevelSmem& ls) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = __reduce_max_sync(FULL, v);
+  if (lane == 0) ls.mx[warp] = v;
   __syncthreads();
-  for (int k = 2; k <= BCELLS; k <<= 1) {        // ascending bitonic sort of unique keys
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const int ixj = t ^ j;
-      if (ixj > t) {
-        const uint32_t a = ls.sk[t], c = ls.sk[ixj];
-        if ((a > c) == ((t & k) == 0)) { ls.sk[t] = c; ls.sk[ixj] = a; }
-      }
-      __syncthreads();
-    }
-  }
-  ls.inv[t] = (uint8_t)(ls.sk[t] & 255u);
+  int m = ls.mx[0];
+  for (int w = 1; w < BCELLS / 32; ++w) m = max(m, ls.mx[w]);
   __syncthreads();
+  return m;
 }
 
 // One CTA (BCELLS threads) lays out brick k0 / BCELLS: its parcels occupy sorted positions
@@ -372,72 +327,76 @@ __device__ __forceinline__ void level_layout(const PArrays<T>& src, const PArray
                                              long long k0, int bs, const int* cs,
                                              const uint32_t* perm, uint8_t* __restrict__ cellmap,
                                              LevelSmem& ls, uint32_t* __restrict__ lperm = nullptr) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (cs[BCELLS] == 0) {                         // an empty brick: own order (never ranked)
-    cellmap[k0 + t] = (uint8_t)t;
+  const int t = threadIdx.x, lane = t & 31;
+  const int u = t & (CT - 1), h = t / CT;        // the cell kernel's thread, level parity
+  if (cs[BCELLS] == 0) {                         // an empty brick: the natural pairing
+    if (t < CT) cellmap[k0 + t] = (uint8_t)(t + CT);
     return;
   }
-  const int cnt = cs[t + 1] - cs[t];
-  // even counts (no empty cell, the largest at most 1.5 x the smallest): ranking cannot
-  // save a quarter of the warp iterations, and is skipped
-  {
-    const int mn = __reduce_min_sync(FULL, cnt), mx = __reduce_max_sync(FULL, cnt);
-    if (lane == 0) { ls.wa[warp] = mn; ls.wb[warp] = mx; }
+  const int total = cs[BCELLS];
+  const int nlo = cs[u + 1] - cs[u];
+  const int nat = nlo + cs[u + CT + 1] - cs[u + CT];
+  const int mx_nat = cta_max(nat, ls);
+  int cB = u + CT;
+  // the count pairing can lower the largest count to about the mean, ceil(total / CT)
+  if (10 * ((total + CT - 1) / CT) < 9 * mx_nat) {  // uniform over the CTA
+    const int cnt = min(cs[t + 1] - cs[t], 0xFFFFFF);
+    ls.sk[t] = t < CT ? ((uint32_t)(0xFFFFFF - cnt) << 8) | (uint32_t)t
+                      : ((uint32_t)cnt << 8) | (uint32_t)t;
     __syncthreads();
-    if (t == 0) {
-      int bmn = ls.wa[0], bmx = ls.wb[0];
-      for (int w = 1; w < BCELLS / 32; ++w) { bmn = min(bmn, ls.wa[w]); bmx = max(bmx, ls.wb[w]); }
-      ls.rank = bmn > 0 && 2 * bmx <= 3 * bmn ? 0 : (bmx < BCELLS ? 1 : 2);
+    // ascending bitonic sort of each half's unique keys (partners t ^ j stay in the half)
+    for (int k = 2; k <= CT; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int ixj = t ^ j;
+        if (ixj > t) {
+          const uint32_t x = ls.sk[t], y = ls.sk[ixj];
+          if ((x > y) == ((u & k) == 0)) { ls.sk[t] = y; ls.sk[ixj] = x; }
+        }
+        __syncthreads();
+      }
     }
+    if (t < CT) ls.pb[ls.sk[t] & 255u] = (uint8_t)(ls.sk[CT + t] & 255u);
     __syncthreads();
+    const int pc = ls.pb[u];
+    const int mx_cnt = cta_max(nlo + cs[pc + 1] - cs[pc], ls);
+    if (10 * mx_cnt < 9 * mx_nat) cB = pc;
   }
-  int cell = t;
-  if (ls.rank) {                                 // uniform over the CTA
-    const int mode = ls.rank;
-    __syncthreads();                             // wa is rewritten by the ranking
-    rank_cells(cnt, mode == 2, ls);
-    // ranked only if it saves more than a quarter of the warp iterations (the sum over
-    // warps of the warp's largest count)
-    const int ct = ls.inv[t];
-    const int rc = cs[ct + 1] - cs[ct];          // count of the cell of rank t
-    const int m_own = __reduce_max_sync(FULL, cnt), m_rank = __reduce_max_sync(FULL, rc);
-    if (lane == 0) { ls.wa[warp] = m_own; ls.wb[warp] = m_rank; }
-    __syncthreads();
-    int sum_own = 0, sum_rank = 0;
-    for (int w = 0; w < BCELLS / 32; ++w) { sum_own += ls.wa[w]; sum_rank += ls.wb[w]; }
-    if (4 * sum_rank < 3 * sum_own) cell = ct;
-    __syncthreads();                             // wa is reused below
-  }
-  cellmap[k0 + t] = (uint8_t)cell;
-  const int c0 = cs[cell];
-  const int n = cs[cell + 1] - c0;
+  if (t < CT) cellmap[k0 + t] = (uint8_t)cB;
+  const int a0 = cs[u], b0 = cs[cB];
+  const int n = nlo + cs[cB + 1] - b0;           // this thread's sequence: a0.., then b0..
   const int ws = __reduce_add_sync(FULL, n);
-  if (lane == 0) ls.wa[warp] = ws;
+  const int kw = (t >> 5) & (CT / 32 - 1);       // the cell kernel's warp
+  if (t < CT && lane == 0) ls.wa[kw] = ws;
   __syncthreads();
   int off = bs;                                  // first parcel of this warp's group
-  for (int w = 0; w < warp; ++w) off += ls.wa[w];
+  for (int w = 0; w < kw; ++w) off += ls.wa[w];
   const int nmax = __reduce_max_sync(FULL, n);
   const unsigned below = (1u << lane) - 1u;
-  // L levels per iteration (4 FP32, 2 FP64), all loads before the stores
+  // L levels of this thread's parity per iteration (4 FP32, 2 FP64), all loads before the
+  // stores; the ballots of both parities give the positions
   constexpr int L = sizeof(T) == 4 ? 4 : 2;
-  for (int r = 0; r < nmax; r += L) {
+  for (int r = 0; r < nmax; r += 2 * L) {
     bool a[L];
     int q[L];
     uint32_t si[L];
     int acc = off;
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-      a[l] = n > r + l;
-      const unsigned bl = __ballot_sync(FULL, a[l]);
-      q[l] = acc + __popc(bl & below);
+    for (int l = 0; l < 2 * L; ++l) {
+      const bool al = n > r + l;
+      const unsigned bl = __ballot_sync(FULL, al);
+      if ((l & 1) == h) {
+        const int rl = r + l;
+        a[l >> 1] = al;
+        q[l >> 1] = acc + __popc(bl & below);
+        si[l >> 1] = al ? perm[rl < nlo ? a0 + rl : b0 + (rl - nlo)] : 0u;
+      }
       acc += __popc(bl);
-      si[l] = a[l] ? perm[c0 + r + l] : 0u;
     }
+    off = acc;
     if (lperm) {                                 // uniform: the permutation only
 #pragma unroll
       for (int l = 0; l < L; ++l)
         if (a[l]) lperm[q[l]] = si[l];
-      off = acc;
       continue;
     }
     T v[L][8];
@@ -460,7 +419,6 @@ __device__ __forceinline__ void level_layout(const PArrays<T>& src, const PArray
         if (src.tag) dst.tag[q[l]] = ig[l];
       }
     }
-    off = acc;
   }
 }
 

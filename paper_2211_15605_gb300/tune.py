@@ -11,7 +11,7 @@ import itertools
 import torch
 
 
-def autotune(bed, parcels: dict, gas, steps: int = 10, grids=(0, 1, 2), sorts=(5, 10, 20),
+def autotune(bed, parcels: dict, gas, steps: int = 10, grids=(0, 2, 3), sorts=(5, 10, 20),
              obj_shape=None):
     """Pick (grid_per_sm, sort_every) for `bed` (mppic.Bed or mppic.Batch) and apply it.
 

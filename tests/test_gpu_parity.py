@@ -89,38 +89,47 @@ def test_binning_bit_exact_including_faces(prec):
 
 
 def check_level_layout(cell, orig, nx, ny, nz):
-    """The layout rule of a sort: each brick's 256 cells are taken 32 at a time, either in
-    their own order or ranked by parcel count (descending, ties by cell index), the latter
-    where it cuts the sum over groups of the group's largest count by more than a quarter
-    (not tried where no cell is empty and the largest count is at most 1.5 times the
-    smallest); the parcels of each group are stored level by level: the r-th parcel of every
-    cell of the group that has one, in group order, then level r+1; within a cell parcels
-    keep their order before the sort (`orig`: each parcel's index before it). Returns which
-    bricks were ranked."""
+    """The layout rule of a sort. The cell kernel runs 128 threads per brick; thread u walks
+    the parcels of two cells, lower-half cell u and an upper-half cell B(u), first those of
+    cell u, then those of B(u). B(u) = u + 128 (the natural pairing), unless pairing by
+    counts lowers the largest per-thread count by more than a tenth (tried only where the
+    natural pairing's largest count exceeds the mean ceil(N/128) by more than a tenth): then
+    the lower-half cells ranked by count descending take the upper-half cells ranked by
+    count ascending (ties by cell index in both). The parcels of each warp (threads
+    32w..32w+31) are stored level by level: the r-th parcel of every thread's sequence that
+    has one, in thread order, then level r+1; within a cell parcels keep their order before
+    the sort (`orig`: each parcel's index before it). Returns which bricks were paired by
+    count."""
     n = cell.size
     i, j, k = cell % nx, (cell // nx) % ny, cell // (nx * ny)
     nbx, nby, nbz = -(-nx // 8), -(-ny // 8), -(-nz // 4)
     brick = (i // 8) + nbx * ((j // 8) + nby * (k // 4))
     local = (i % 8) + 8 * ((j % 8) + 8 * (k % 4))
     key = brick * 256 + local
-    # rank of each cell within its brick: by count descending, then cell index
     counts = np.bincount(key, minlength=nbx * nby * nbz * 256).reshape(-1, 256)
-    idx = np.broadcast_to(np.arange(256), counts.shape)
-    order = np.lexsort((idx, -counts), axis=-1)
-    rank = np.empty_like(order)
-    np.put_along_axis(rank, order, np.broadcast_to(np.arange(256), order.shape), axis=-1)
-    it_own = counts.reshape(-1, 8, 32).max(axis=2).sum(axis=1)
-    it_rank = np.take_along_axis(counts, order, axis=-1).reshape(-1, 8, 32).max(axis=2).sum(axis=1)
-    even = (counts.min(axis=1) > 0) & (2 * counts.max(axis=1) <= 3 * counts.min(axis=1))
-    ranked = ~even & (4 * it_rank < 3 * it_own)
-    rank = np.where(ranked[:, None], rank, idx)
-    rk = rank[brick, local]
+    lo, up = counts[:, :128], counts[:, 128:]
+    mx_nat = (lo + up).max(axis=1)
+    tot = counts.sum(axis=1)
+    tried = 10 * (-(-tot // 128)) < 9 * mx_nat
+    idx = np.broadcast_to(np.arange(128), lo.shape)
+    olo = np.lexsort((idx, -lo), axis=-1)          # lower half: count descending, then index
+    oup = np.lexsort((idx, up), axis=-1)           # upper half: count ascending, then index
+    pb = np.empty_like(olo)
+    np.put_along_axis(pb, olo, oup + 128, axis=-1)
+    mx_cnt = (lo + np.take_along_axis(counts, pb, axis=-1)).max(axis=1)
+    paired = tried & (10 * mx_cnt < 9 * mx_nat)
+    B = np.where(paired[:, None], pb, idx + 128)
+    inv = np.empty_like(B)                         # thread of each upper-half cell
+    np.put_along_axis(inv, B - 128, idx, axis=-1)
     # rank of each parcel within its cell, in the order before the sort
     o = np.lexsort((orig, key))
     first = np.searchsorted(key[o], key[o], side="left")
     lvl = np.empty(n, np.int64)
     lvl[o] = np.arange(n) - first
-    t = np.stack([brick, rk // 32, lvl, rk], axis=1)
+    upper = local >= 128
+    u = np.where(upper, inv[brick, np.where(upper, local - 128, 0)], local)
+    s = np.where(upper, counts[brick, u] + lvl, lvl)
+    t = np.stack([brick, u // 32, s, u], axis=1)
     d = np.diff(t, axis=0)
     inc = np.zeros(len(d), bool)
     eq = np.ones(len(d), bool)
@@ -128,7 +137,7 @@ def check_level_layout(cell, orig, nx, ny, nz):
         inc |= eq & (d[:, c] > 0)
         eq &= d[:, c] == 0
     assert np.all(inc)
-    return ranked
+    return paired
 
 
 @pytest.mark.parametrize("prec", [32, 64])
@@ -141,8 +150,8 @@ def test_sort_is_a_stable_level_permutation(prec):
     pid = dev["pid"].cpu().numpy()
     assert np.array_equal(np.sort(pid), np.arange(bed.np))
     np.testing.assert_array_equal(host(dev["x"]), x0[pid])        # arrays moved together
-    ranked = check_level_layout(dev["cell"].cpu().numpy(), pid, 20, 12, 9)
-    assert ranked.any() and not ranked.all()       # the bed exercises both choices
+    paired = check_level_layout(dev["cell"].cpu().numpy(), pid, 20, 12, 9)
+    assert paired.any() and not paired.all()       # the bed exercises both choices
 
 
 FIELDS = ("x", "y", "z", "u", "v", "w", "d", "omega", "pid")
