@@ -486,6 +486,7 @@ constexpr int CT = BCELLS / 2;
 //   fx   [NQ][W][TNODES] u64: exact fixed-point sums (parcels off their sorted cell; in the
 //        FP32 form also the exact volume of the cells' own parcels);
 //   tile [NQ][TNODES] T: the node sums of the cells' own parcels (after the parcel loop);
+//        during the loop, each warp's queue of 32 parcel records for the off-cell deposits;
 //   cbuf [NQ*8][CT] T and [CT] long long: the 40 corner sums (and exact volume) a thread's
 //        first cell leaves when the thread moves on to its second.
 template <class T>
@@ -498,6 +499,7 @@ struct CellSmem {
   __host__ __device__ static constexpr size_t bytes(bool gp) { return vbuf(gp) + sizeof(long long) * CT; }
 };
 static_assert(sizeof(float) * 3 * CT <= sizeof(float) * 5 * TNODES, "objective partials fit the tile");
+static_assert(8 * 32 * (CT / 32) <= NQ * TNODES, "the warps' off-cell queues fit the node tile");
 
 // Asynchronous copy of one parcel value into this thread's prefetch slot.
 __device__ __forceinline__ void cp_async(float* dst, const float* src) {
@@ -514,50 +516,76 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// A parcel record of the off-cell queue: cell (pack_cell), in-cell coordinates, up to 4
+// values, 8 values of T (the cell id's bits in the FP32 form, its value in the FP64 form).
+__device__ __forceinline__ float cell_as_t(int c, float) { return __int_as_float(c); }
+__device__ __forceinline__ double cell_as_t(int c, double) { return (double)c; }
+__device__ __forceinline__ int cell_of_t(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int cell_of_t(double v) { return (int)v; }
+__device__ __forceinline__ void store_rec(float* r, const float (&v)[8]) {
+  reinterpret_cast<float4*>(r)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(r)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void store_rec(double* r, const double (&v)[8]) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) reinterpret_cast<double2*>(r)[h] = make_double2(v[2 * h], v[2 * h + 1]);
+}
+__device__ __forceinline__ void load_rec(const float* r, float (&v)[8]) {
+  const float4 a = reinterpret_cast<const float4*>(r)[0], b = reinterpret_cast<const float4*>(r)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void load_rec(const double* r, double (&v)[8]) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const double2 d = reinterpret_cast<const double2*>(r)[h];
+    v[2 * h] = d.x; v[2 * h + 1] = d.y;
+  }
+}
+
 // Adds NV values at the 8 corners of cell `cell` (pack_cell) with in-cell coordinates x0..x2 in exact
 // fixed point, starting at quantity q0 (0 = Vs, 1 = A, then Bx, By, Bz), for every lane of
 // the warp in `pend` (a ballot, not 0; all 32 lanes call it): into the brick's shared tile
 // if the cell is in the brick (i0, j0, k0 = its first cell), else into the global
 // accumulators. Used for parcels that are not in their sorted cell. These are rare, so the
-// warp shares the work: in rounds of four such lanes, lanes 8g..8g+7 take the 8 corners of
-// the g-th, instead of each lane running its 8 corners while the rest of the warp idles.
-// Integer additions commute, so neither the order of these calls nor the rounds change any
-// sum. EXACT (the solids volume of the FP32 form): the corner with the largest weight adds
-// the parcel's volume in fixed point minus the other seven corners' values, so that the 8
-// corners add up to exactly the parcel's volume (v0 * mV is exact: mV is a power of two).
+// warp shares the work: each such lane queues its parcel in wq (the warp's 32 records of 8
+// values, 16-byte aligned) at its rank among them; in rounds of four, lanes 8g..8g+7 take the
+// 8 corners of record 4r+g, instead of each lane running its 8 corners while the rest of the
+// warp idles. Integer additions commute, so neither the order of these calls nor the rounds
+// change any sum. EXACT (the solids volume of the FP32 form): the corner with the largest
+// weight adds the parcel's volume in fixed point minus the other seven corners' values, so
+// that the 8 corners add up to exactly the parcel's volume (v0 * mV is exact: mV is a power
+// of two).
 template <class T, int NV, bool EXACT = false>
 __device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* fx, int* kr, int i0,
                                                   int j0, int k0, unsigned pend, CellBits cb, int cell, T x0, T x1,
-                                                  T x2, int q0, T v0, T v1, T v2, T v3) {
+                                                  T x2, int q0, T v0, T v1, T v2, T v3, T* wq) {
   constexpr int W = Words<T>::n;
   const int lane = threadIdx.x & 31, g = lane >> 3, corner = lane & 7;
   const int a = corner & 1, b = (corner >> 1) & 1, c = corner >> 2;
-  while (pend) {
-    unsigned m = pend;                           // the g-th lowest pending lane
-    for (int t = 0; t < g; ++t) m &= m - 1u;
-    const bool has = m != 0u;
-    const int s = has ? __ffs(m) - 1 : 0;
+  if ((pend >> lane) & 1u) {
+    const T rec[8] = {cell_as_t(cell, T(0)), x0, x1, x2, v0, v1, v2, v3};
+    store_rec(wq + 8 * __popc(pend & ((1u << lane) - 1u)), rec);
+  }
+  __syncwarp();
+  const int npend = __popc(pend);
+  for (int k = g; k - g < npend; k += 4) {
+    const bool has = k < npend;
+    T rec[8];
+    load_rec(wq + 8 * (has ? k : 0), rec);
     int si, sj, sk;
-    unpack_cell(p, cb, __shfl_sync(FULL, cell, s), si, sj, sk);
-    const T y0 = __shfl_sync(FULL, x0, s), y1 = __shfl_sync(FULL, x1, s), y2 = __shfl_sync(FULL, x2, s);
-    T vals[4];
-    vals[0] = __shfl_sync(FULL, v0, s);
-    if (NV > 1) {
-      vals[1] = __shfl_sync(FULL, v1, s);
-      vals[2] = __shfl_sync(FULL, v2, s);
-      vals[3] = __shfl_sync(FULL, v3, s);
-    }
+    unpack_cell(p, cb, cell_of_t(rec[0]), si, sj, sk);
+    const T y0 = rec[1], y1 = rec[2], y2 = rec[3];
     const T Wq = ((a ? y0 : T(1) - y0) * (b ? y1 : T(1) - y1)) * (c ? y2 : T(1) - y2);
     u64 fe[W] = {};
     if (EXACT) {                                 // all 32 lanes: the group sum of the others
       const int kst = (y0 >= T(0.5) ? 1 : 0) + (y1 >= T(0.5) ? 2 : 0) + (y2 >= T(0.5) ? 4 : 0);
-      to_fixed(has ? vals[0] * Wq : T(0), p.mV, fe, p.errs);
+      to_fixed(has ? rec[4] * Wq : T(0), p.mV, fe, p.errs);
       long long others = corner == kst ? 0ll : (long long)fe[0];
 #pragma unroll
       for (int o = 1; o < 8; o <<= 1) others += __shfl_xor_sync(FULL, others, o);
       if (corner == kst) {
         u64 tot[W];
-        to_fixed(has ? vals[0] : T(0), p.mV, tot, p.errs);
+        to_fixed(has ? rec[4] : T(0), p.mV, tot, p.errs);
         fe[0] = (u64)((long long)tot[0] - others);
       }
     }
@@ -575,7 +603,7 @@ __device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* f
         if (EXACT) {
           f[0] = fe[0];
         } else {
-          to_fixed(vals[v] * Wq, qq == 0 ? p.mV : p.mA, f, p.errs);
+          to_fixed(rec[4 + v] * Wq, qq == 0 ? p.mV : p.mA, f, p.errs);
         }
         if (in)
           acc_add(fx + (qq * W) * TNODES + (ti + a) + TX * ((tj + b) + TY * (tk + c)), TNODES, f);
@@ -584,8 +612,8 @@ __device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* f
                   p.nstride, f);
       }
     }
-    for (int t = 0; t < 4; ++t) pend &= pend - 1u;
   }
+  __syncwarp();                                  // the queue is reused by the next call
 }
 
 // Trilinear corner weights W[a + 2b + 4c] of in-cell coordinates xi. FP64: 8 values. FP32:
@@ -978,6 +1006,7 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   T* cbuf = reinterpret_cast<T*>(smem + S::cbuf(gpl));  // sums of each thread's first cell
   long long* vbuf = reinterpret_cast<long long*>(smem + S::vbuf(gpl));
   T* red = sf;                                     // after the parcel loop: objective partials
+  T* wq = tile + 8 * 32 * (threadIdx.x >> 5);      // during the parcel loop: the warp's off-cell queue
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -1201,15 +1230,15 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
       if (po) {
         if (MODE == MODE_VOLUME)
           deposit_foreign_warp<T, 1, EXACT_V>(p, fx, s_kr, bi0, bj0, bk0, po, cb, co, xo[0], xo[1], xo[2],
-                                              0, V, T(0), T(0), T(0));
+                                              0, V, T(0), T(0), T(0), wq);
         else
           deposit_foreign_warp<T, 4>(p, fx, s_kr, bi0, bj0, bk0, po, cb, co, xo[0], xo[1], xo[2], 1, fd[0],
-                                     fd[1], fd[2], fd[3]);
+                                     fd[1], fd[2], fd[3], wq);
       }
       const unsigned pn = MODE == MODE_STEP ? __ballot_sync(FULL, off_new) : 0u;
       if (pn)
         deposit_foreign_warp<T, 1, EXACT_V>(p, fx, s_kr, bi0, bj0, bk0, pn, cb, cno, xno[0], xno[1], xno[2],
-                                            0, V, T(0), T(0), T(0));
+                                            0, V, T(0), T(0), T(0), wq);
     }
     off += __popc(bal);
   }
