@@ -208,15 +208,14 @@ FP64_FLOPS_PER_PARCEL = 602
 FP64_FLOPS_SOURCE = "ncu counters: (DADD + DMUL + 2 DFMA) / parcels of one launch, 8M-parcel dense bed"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32 step kernel per
-# parcel, from ncu captures on the 128x128x128 / 8M-parcel dense bed sorted every 2 steps:
-# 65.4 B at step 150 (the fluidised bed, as in the timed window; 58.9 B at step 5), in
-# proportion to the parcels. Reported only while the kernel source is the one captured.
+# parcel, from ncu captures on the 128x128x128 / 8M-parcel dense bed sorted every 2 steps,
+# in proportion to the parcels. Reported only while the kernel source is the one captured.
 STEP_TRAFFIC = {"workload": "dense", "precision": 32,
                 # DRAM bytes per parcel of one launch of each step-kernel instance, ncu on the
                 # 8M-parcel dense bed at step 150: a step that updates the values in place, and
                 # a step after a sort that reads them through the sort's permutation
-                "in_place_bytes_per_parcel": 61.9, "perm_bytes_per_parcel": 70.5,
-                "source_sha256": "8e8b305067b0a525973af8e9fb183cd3965435ff901e6c7a69f4fe8d70f74ca9"}
+                "in_place_bytes_per_parcel": 61.9, "perm_bytes_per_parcel": 70.8,
+                "source_sha256": "25e79b2f100909897bb23be893ffcf667f3b941657adf93c26c2292c8fd9bdf2"}
 
 
 def step_traffic(args, np_, start):
