@@ -486,7 +486,8 @@ constexpr int CT = BCELLS / 2;
 //   fx   [NQ][W][TNODES] u64: exact fixed-point sums (parcels off their sorted cell; in the
 //        FP32 form also the exact volume of the cells' own parcels);
 //   tile [NQ][TNODES] T: the node sums of the cells' own parcels (after the parcel loop);
-//        during the loop, each warp's queue of 32 parcel records for the off-cell deposits;
+//        during the loop, each warp's two queues of QCAP parcel records for the off-cell
+//        deposits;
 //   cbuf [NQ*8][CT] T and [CT] long long: the 40 corner sums (and exact volume) a thread's
 //        first cell leaves when the thread moves on to its second.
 template <class T>
@@ -494,12 +495,14 @@ struct CellSmem {
   static constexpr int W = Words<T>::n;
   __host__ __device__ static constexpr size_t fx(bool gp) { return rup(sizeof(T) * tile_vals(gp) * TNODES, 128); }
   __host__ __device__ static constexpr size_t tile(bool gp) { return rup(fx(gp) + sizeof(u64) * NQ * W * TNODES, 128); }
-  __host__ __device__ static constexpr size_t cbuf(bool gp) { return rup(tile(gp) + sizeof(T) * NQ * TNODES, 128); }
+  // the warps' off-cell queues, two of QCAP records of 8 values per warp, share the tile
+  static constexpr int QCAP = 32;
+  static constexpr size_t tile_len = NQ * TNODES > 2 * QCAP * 8 * (CT / 32) ? NQ * TNODES : 2 * QCAP * 8 * (CT / 32);
+  __host__ __device__ static constexpr size_t cbuf(bool gp) { return rup(tile(gp) + sizeof(T) * tile_len, 128); }
   __host__ __device__ static constexpr size_t vbuf(bool gp) { return cbuf(gp) + sizeof(T) * NQ * 8 * CT; }
   __host__ __device__ static constexpr size_t bytes(bool gp) { return vbuf(gp) + sizeof(long long) * CT; }
 };
 static_assert(sizeof(float) * 3 * CT <= sizeof(float) * 5 * TNODES, "objective partials fit the tile");
-static_assert(8 * 32 * (CT / 32) <= NQ * TNODES, "the warps' off-cell queues fit the node tile");
 
 // Asynchronous copy of one parcel value into this thread's prefetch slot.
 __device__ __forceinline__ void cp_async(float* dst, const float* src) {
@@ -542,32 +545,42 @@ __device__ __forceinline__ void load_rec(const double* r, double (&v)[8]) {
   }
 }
 
-// Adds NV values at the 8 corners of cell `cell` (pack_cell) with in-cell coordinates x0..x2 in exact
-// fixed point, starting at quantity q0 (0 = Vs, 1 = A, then Bx, By, Bz), for every lane of
-// the warp in `pend` (a ballot, not 0; all 32 lanes call it): into the brick's shared tile
-// if the cell is in the brick (i0, j0, k0 = its first cell), else into the global
-// accumulators. Used for parcels that are not in their sorted cell. These are rare, so the
-// warp shares the work: each such lane queues its parcel in wq (the warp's 32 records of 8
-// values, 16-byte aligned) at its rank among them; in rounds of four, lanes 8g..8g+7 take the
-// 8 corners of record 4r+g, instead of each lane running its 8 corners while the rest of the
-// warp idles. Integer additions commute, so neither the order of these calls nor the rounds
-// change any sum. EXACT (the solids volume of the FP32 form): the corner with the largest
-// weight adds the parcel's volume in fixed point minus the other seven corners' values, so
-// that the 8 corners add up to exactly the parcel's volume (v0 * mV is exact: mV is a power
-// of two).
+// Off-cell deposits. Parcels that are not in their sorted cell add their contributions in
+// exact fixed point: NV values at the 8 corners of cell `cell` (pack_cell) with in-cell
+// coordinates x0..x2, starting at quantity q0 (0 = Vs, 1 = A, then Bx, By, Bz), into the
+// brick's shared tile if the cell is in the brick (i0, j0, k0 = its first cell), else into
+// the global accumulators. These are a few percent of the parcels, so the warp shares the
+// work: the lanes with such a parcel queue a record of it (queue_offcell) in the warp's
+// queue, and when the next records would not fit (and after the loop) the whole warp drains it
+// (drain_offcell) in rounds of four records, lanes 8g..8g+7 taking the 8 corners of record
+// 4r+g, instead of each lane running its 8 corners while the rest of the warp idles.
+// Integer additions commute, so neither when a record is drained nor the rounds change any
+// sum. EXACT (the solids volume of the FP32 form): the corner with the largest weight adds
+// the parcel's volume in fixed point minus the other seven corners' values, so that the 8
+// corners add up to exactly the parcel's volume (v0 * mV is exact: mV is a power of two).
+
+// Appends a record for every lane in `pend` (a ballot; all 32 lanes call it) to the warp's
+// queue wq (16-byte aligned records of 8 values) holding n records; returns the new count.
+template <class T>
+__device__ __forceinline__ int queue_offcell(T* wq, int n, unsigned pend, int cell, T x0, T x1, T x2,
+                                             T v0, T v1, T v2, T v3) {
+  const int lane = threadIdx.x & 31;
+  if ((pend >> lane) & 1u) {
+    const T rec[8] = {cell_as_t(cell, T(0)), x0, x1, x2, v0, v1, v2, v3};
+    store_rec(wq + 8 * (n + __popc(pend & ((1u << lane) - 1u))), rec);
+  }
+  return n + __popc(pend);
+}
+
+// Deposits the warp's npend queued records (all 32 lanes call it, npend uniform) and empties
+// the queue.
 template <class T, int NV, bool EXACT = false>
-__device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* fx, int* kr, int i0,
-                                                  int j0, int k0, unsigned pend, CellBits cb, int cell, T x0, T x1,
-                                                  T x2, int q0, T v0, T v1, T v2, T v3, T* wq) {
+__device__ __forceinline__ void drain_offcell(const KParams<T>& p, u64* fx, int* kr, int i0, int j0,
+                                              int k0, CellBits cb, int q0, const T* wq, int npend) {
   constexpr int W = Words<T>::n;
   const int lane = threadIdx.x & 31, g = lane >> 3, corner = lane & 7;
   const int a = corner & 1, b = (corner >> 1) & 1, c = corner >> 2;
-  if ((pend >> lane) & 1u) {
-    const T rec[8] = {cell_as_t(cell, T(0)), x0, x1, x2, v0, v1, v2, v3};
-    store_rec(wq + 8 * __popc(pend & ((1u << lane) - 1u)), rec);
-  }
-  __syncwarp();
-  const int npend = __popc(pend);
+  __syncwarp();                                  // the records are written
   for (int k = g; k - g < npend; k += 4) {
     const bool has = k < npend;
     T rec[8];
@@ -613,7 +626,7 @@ __device__ __forceinline__ void deposit_foreign_warp(const KParams<T>& p, u64* f
       }
     }
   }
-  __syncwarp();                                  // the queue is reused by the next call
+  __syncwarp();                                  // the queue is refilled after this
 }
 
 // Trilinear corner weights W[a + 2b + 4c] of in-cell coordinates xi. FP64: 8 values. FP32:
@@ -1006,7 +1019,10 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   T* cbuf = reinterpret_cast<T*>(smem + S::cbuf(gpl));  // sums of each thread's first cell
   long long* vbuf = reinterpret_cast<long long*>(smem + S::vbuf(gpl));
   T* red = sf;                                     // after the parcel loop: objective partials
-  T* wq = tile + 8 * 32 * (threadIdx.x >> 5);      // during the parcel loop: the warp's off-cell queue
+  // the warp's off-cell queues (old position, new position): records of 8 values
+  constexpr int QCAP = S::QCAP;
+  T* q_old = tile + (threadIdx.x >> 5) * 2 * QCAP * 8;
+  T* q_new = q_old + QCAP * 8;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -1077,6 +1093,14 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   sums.zero();
   long long vtot = 0;                            // EXACT_V: the current cell's volume, fixed point
   T o_dp = 0, o_hn = 0, o_vs = 0;
+  int n_old = 0, n_new = 0;                      // records in the warp's off-cell queues
+  auto drain_old = [&]() {
+    if (MODE == MODE_VOLUME)
+      drain_offcell<T, 1, EXACT_V>(p, fx, s_kr, bi0, bj0, bk0, cb, 0, q_old, n_old);
+    else
+      drain_offcell<T, 4>(p, fx, s_kr, bi0, bj0, bk0, cb, 1, q_old, n_old);
+  };
+  auto drain_new = [&]() { drain_offcell<T, 1, EXACT_V>(p, fx, s_kr, bi0, bj0, bk0, cb, 0, q_new, n_new); };
 
   // Level r+1's parcel values are loaded into registers (nv) while level r is processed, so
   // that their latency is covered by one iteration. PERM (the step after a sort that wrote
@@ -1225,23 +1249,25 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
         }
       }
     }
-    {
+    {                            // queue the parcels off their cell (a full queue is drained first)
       const unsigned po = __ballot_sync(FULL, off_old);
       if (po) {
+        if (n_old + __popc(po) > QCAP) { drain_old(); n_old = 0; }
         if (MODE == MODE_VOLUME)
-          deposit_foreign_warp<T, 1, EXACT_V>(p, fx, s_kr, bi0, bj0, bk0, po, cb, co, xo[0], xo[1], xo[2],
-                                              0, V, T(0), T(0), T(0), wq);
+          n_old = queue_offcell(q_old, n_old, po, co, xo[0], xo[1], xo[2], V, T(0), T(0), T(0));
         else
-          deposit_foreign_warp<T, 4>(p, fx, s_kr, bi0, bj0, bk0, po, cb, co, xo[0], xo[1], xo[2], 1, fd[0],
-                                     fd[1], fd[2], fd[3], wq);
+          n_old = queue_offcell(q_old, n_old, po, co, xo[0], xo[1], xo[2], fd[0], fd[1], fd[2], fd[3]);
       }
       const unsigned pn = MODE == MODE_STEP ? __ballot_sync(FULL, off_new) : 0u;
-      if (pn)
-        deposit_foreign_warp<T, 1, EXACT_V>(p, fx, s_kr, bi0, bj0, bk0, pn, cb, cno, xno[0], xno[1], xno[2],
-                                            0, V, T(0), T(0), T(0), wq);
+      if (pn) {
+        if (n_new + __popc(pn) > QCAP) { drain_new(); n_new = 0; }
+        n_new = queue_offcell(q_new, n_new, pn, cno, xno[0], xno[1], xno[2], V, T(0), T(0), T(0));
+      }
     }
     off += __popc(bal);
   }
+  if (n_old) drain_old();
+  if (n_new) drain_new();
   // ---- node layers of this brick's own-cell deposits (off-cell deposits recorded theirs
   // as they were made); merged into the global range below, for the next finalize
   const int ckA = bk0 + tid / (BX * BY), ckB = bk0 + lcB / (BX * BY);
