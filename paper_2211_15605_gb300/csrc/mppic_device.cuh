@@ -1077,9 +1077,8 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
       }
     }
     cp_async_commit();
-    cp_async_wait<0>();
   }
-  __syncthreads();
+  __syncthreads();                               // the warps' parcel counts are written
 
   // the cell whose parcels the thread walks (the first one with parcels), and sw: the level
   // at which it moves on to the second (-1: it does not)
@@ -1129,8 +1128,11 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
     pf_off += __popc(bl);
     if (PERM && lv + 1 < nmax) pf_src = perm_at(lv + 1, pf_off);
   };
+  // the first level's loads are in flight while the node-field tile completes
   if (PERM && nmax > 0) pf_src = perm_at(0, pf_off);
   if (nmax > 0) load_level(0);
+  if (MODE != MODE_VOLUME) cp_async_wait<0>();
+  __syncthreads();                               // the node-field tile is complete
   for (int r = 0; r < nmax; ++r) {
     T cv[8];
 #pragma unroll
@@ -1360,12 +1362,16 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   if (MODE == MODE_STEP) cta_sum3<CT / 32>(o_dp, o_hn, o_vs, red, obj_part + 3 * b);
   };  // one brick
 
-  for (long long iter = 0; iter < total_bricks; ++iter) {
+  // thread 0 takes the next brick from the work counter while the current one runs
+  long long next = 0;
+  if (tid == 0) next = (long long)atomicAdd(work, 1ull);
+  for (long long iter = 0; iter <= total_bricks; ++iter) {
     __syncthreads();
-    if (tid == 0) s_brick = (long long)atomicAdd(work, 1ull);
+    if (tid == 0) s_brick = next;
     __syncthreads();
     const long long b = s_brick;
     if (b >= total_bricks) break;
+    if (tid == 0) next = (long long)atomicAdd(work, 1ull);
     if (BATCH) {
       const int bed = brick_bed[b];
       if (bed != cur_bed) {
