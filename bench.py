@@ -214,8 +214,8 @@ STEP_TRAFFIC = {"workload": "dense", "precision": 32,
                 # DRAM bytes per parcel of one launch of each step-kernel instance, ncu on the
                 # 8M-parcel dense bed at step 150: a step that updates the values in place, and
                 # a step after a sort that reads them through the sort's permutation
-                "in_place_bytes_per_parcel": 61.9, "perm_bytes_per_parcel": 70.8,
-                "source_sha256": "25e79b2f100909897bb23be893ffcf667f3b941657adf93c26c2292c8fd9bdf2"}
+                "in_place_bytes_per_parcel": 61.8, "perm_bytes_per_parcel": 70.8,
+                "source_sha256": "f8fbf0ab8f4cd842e4084a14b2f60d723dbdf678f39d3e21ed63c4ea784be0bc"}
 
 
 def step_traffic(args, np_, start):
