@@ -159,17 +159,19 @@ __device__ __forceinline__ bool xi_in_cell(float x, double, float inv_f, float i
 }
 
 // Binning of (x, y, z) when cell (i, j, k) is the likely answer: the in-cell test on each
-// axis, and the full formula only where it fails. Returns whether the cell is (i, j, k).
+// axis, and the full formula only on the axes where it fails (where the test passes, the
+// formula gives the same index and in-cell coordinate). Returns whether the cell is (i, j, k).
 template <class T>
 __device__ __forceinline__ bool bin3_expect(const KParams<T>& p, T x, T y, T z, int i, int j, int k,
                                             Cell3<T>& c) {
-  if (xi_in_cell(x, p.inv_d[0], p.inv_f[0], p.inv_lo[0], i, c.xi[0]) &&
-      xi_in_cell(y, p.inv_d[1], p.inv_f[1], p.inv_lo[1], j, c.xi[1]) &&
-      xi_in_cell(z, p.inv_d[2], p.inv_f[2], p.inv_lo[2], k, c.xi[2])) {
-    c.i = i; c.j = j; c.k = k;
-    return true;
-  }
-  bin3(p, x, y, z, c);
+  const bool ox = xi_in_cell(x, p.inv_d[0], p.inv_f[0], p.inv_lo[0], i, c.xi[0]);
+  const bool oy = xi_in_cell(y, p.inv_d[1], p.inv_f[1], p.inv_lo[1], j, c.xi[1]);
+  const bool oz = xi_in_cell(z, p.inv_d[2], p.inv_f[2], p.inv_lo[2], k, c.xi[2]);
+  c.i = i; c.j = j; c.k = k;
+  if (ox && oy && oz) return true;
+  if (!ox) bin_axis(x, p.inv_d[0], p.inv_f[0], p.inv_lo[0], p.nx, c.i, c.xi[0]);
+  if (!oy) bin_axis(y, p.inv_d[1], p.inv_f[1], p.inv_lo[1], p.ny, c.j, c.xi[1]);
+  if (!oz) bin_axis(z, p.inv_d[2], p.inv_f[2], p.inv_lo[2], p.nz, c.k, c.xi[2]);
   return c.i == i && c.j == j && c.k == k;
 }
 
