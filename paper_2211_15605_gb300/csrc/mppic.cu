@@ -252,6 +252,8 @@ KParams<T> make_params(const mppic_handle* h, const mppic_gas* gas) {
   p.kS2 = (T)(c.mu_g / c.rho_g);
   p.drag_model = c.drag_model;
   fixed_units(c, sizeof(T), &p.mV, &p.mA);
+  p.inv_vcell = 1.0 / p.vcell;
+  p.es_scale = (float)(1.0 / (double)p.mV / p.vcell);
   p.inv_mV = 1.0 / (double)p.mV; p.inv_mA = 1.0 / (double)p.mA;
   T* f = static_cast<T*>(h->fld);
   for (int k = 0; k < 5; ++k) p.fld[k] = f + (long long)k * h->nnode;
@@ -567,12 +569,12 @@ mppic_status launch_cells_b(mppic_handle* h, const KParams<T>& p, PArrays<T> src
 }
 
 // A batch (beds != NULL) takes the instance that reads each bed's parameters from `beds`;
-// src.perm set (a step after a sort that wrote only the permutation) the instance that reads
-// its parcels through it.
+// src.perm set (a step or volume deposit after a sort that wrote only the permutation) the
+// instance that reads its parcels through it.
 template <class T, int MODE, int DRAG>
 mppic_status launch_cells_t(mppic_handle* h, const KParams<T>& p, PArrays<T> src, PArrays<T> dst,
                             int* cell_out, long long np, const KParams<T>* beds, uint32_t* key_out) {
-  if constexpr (MODE == MODE_STEP)
+  if constexpr (MODE != MODE_DRAG)
     if (src.perm)
       return beds ? launch_cells_b<T, MODE, DRAG, true, true>(h, p, src, dst, cell_out, np, beds, key_out)
                   : launch_cells_b<T, MODE, DRAG, false, true>(h, p, src, dst, cell_out, np, beds, key_out);
@@ -698,8 +700,9 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   // the values are in the copy); a step without a sort updates the values where they are,
   // and the copy's values go back to the caller's arrays once, after the last step. Taken
   // where no identity array travels with the parcels and no gas iteration reads them before
-  // the step. A re-sort at the call's start then follows the call's volume deposit, which
-  // reads the arrays in the last sort's layout (its integer sums do not depend on the order).
+  // the step. A re-sort at the call's start does the same, and the call's volume deposit
+  // then reads the parcels through its permutation, as the gathered path reads the moved
+  // values: both group the parcels by their new cells, so their sums agree bit for bit.
   const bool perm_sort = !ck && !pc->pid && h->cfg.coupling_iters == 0;
   bool start_perm = false;
   if (!h->order_on_caller || h->order_np != np || sort_due(h->step_counter)) {
@@ -718,13 +721,13 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   if (s) return s;
   s = clear_volume_accumulator(h);
   if (s) return s;
-  s = launch_cells<T>(h, MODE_VOLUME, p, src, src, nullptr, pc->np, beds);   // Vs of the current positions
-  if (s) return s;
   if (start_perm) {
     s = sort_into_scratch<T>(h, pc, caller, false, true, gas, true);
     if (s) return s;
     src.perm = h->lperm;
   }
+  s = launch_cells<T>(h, MODE_VOLUME, p, src, src, nullptr, pc->np, beds);   // Vs of the current positions
+  if (s) return s;
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   const PArrays<T> copy = sorted_arrays<T>(h, false, false);
   bool in_copy = start_perm;                     // the values are (step 0: go) in the handle's copy

@@ -57,6 +57,8 @@ struct KParams {
   T invh[3];                 // 1/h in T (interpolant gradient)
   T L[3];
   double vcell;
+  double inv_vcell;          // 1 / vcell
+  float es_scale;            // FP32 form: cell volume fraction per fixed-point unit, inv_mV / vcell
   T rho_g, mu_g, g[3], gp[3], rho_p, Ps, beta, eps_cp, alpha, eg_min, e_wall, C, sd, dt;
   T vcoef;                   // pi/6 * s_d^3: V = w d^3 vcoef
   T inv_rho_p;               // 1 / rho_p
@@ -1104,8 +1106,9 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
   auto drain_new = [&]() { drain_offcell<T, 1, EXACT_V>(p, fx, s_kr, bi0, bj0, bk0, cb, 0, q_new, n_new); };
 
   // Level r+1's parcel values are loaded into registers (nv) while level r is processed, so
-  // that their latency is covered by one iteration. PERM (the step after a sort that wrote
-  // only the permutation): the values of layout position q are read from index src.perm[q];
+  // that their latency is covered by one iteration. PERM (a step or volume deposit after a
+  // sort that wrote only the permutation): the values of layout position q are read from
+  // index src.perm[q];
   // each level's load also fetches the next level's index, one iteration ahead of its use.
   int pf_off = off;                              // first position of the next level to load
   uint32_t pf_src = 0;                           // PERM: this thread's index in that level
@@ -1496,23 +1499,27 @@ __device__ __forceinline__ void finalize_node(const KParams<T>& p, int ep, int n
   u64 fx[W];
   node_sum(p, ep, 0, n, i, j, k, fx);
   if (W == 1 && (long long)fx[0] >= (1ll << 62)) atomicOr(p.errs, ERR_RANGE);
-  double Vs = from_fixed(fx, p.inv_mV);
   for (int e = 0; e < NQ * W; ++e) p.acc[(long long)e * p.nstride + p.nbase + n] = 0;
-  if (vs_out) vs_out[n] = Vs;
-  double vn = p.vcell;
-  if (i == 0 || i == p.nx) vn *= 0.5;
-  if (j == 0 || j == p.ny) vn *= 0.5;
-  if (k == 0 || k == p.nz) vn *= 0.5;
-  T es = (T)(Vs / vn);
+  if (vs_out) vs_out[n] = from_fixed(fx, p.inv_mV);
+  // the node's control volume is the cell volume halved once per boundary axis: eps_s is
+  // Vs / V_n = Vs 2^nb / vcell, formed with a product (the FP32 form in FP32 from the integer:
+  // the FP64 pipe is narrow on GB300, and a division per node made it this pass's bound)
+  const int nb = (i == 0 || i == p.nx) + (j == 0 || j == p.ny) + (k == 0 || k == p.nz);
+  T es;
+  if (W == 1)
+    es = (T)((float)(long long)fx[0] * (p.es_scale * (float)(1 << nb)));
+  else
+    es = (T)(from_fixed(fx, p.inv_mV) * (p.inv_vcell * (double)(1 << nb)));
   T eg = T(1) - es;
   T egc = tmax(eg, p.eg_min);
+  const T iegc = T(1) / egc;
   T U0 = p.U[0] ? p.U[0][n] : T(0);
   T U1 = p.U[1] ? p.U[1][n] : T(0);
   T U2 = (p.U[2] ? p.U[2][n] : T(0)) + p.u_in;
   p.fld[0][n] = es;
-  p.fld[1][n] = U0 / egc;
-  p.fld[2][n] = U1 / egc;
-  p.fld[3][n] = U2 / egc;
+  p.fld[1][n] = U0 * iegc;
+  p.fld[2][n] = U1 * iegc;
+  p.fld[3][n] = U2 * iegc;
   T den = tmax(p.eps_cp - es, p.alpha * (T(1) - es));
   p.fld[4][n] = p.Ps * tpow(es, p.beta) / den;
 }
