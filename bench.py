@@ -215,7 +215,7 @@ STEP_TRAFFIC = {"workload": "dense", "precision": 32,
                 # 8M-parcel dense bed at step 150: a step that updates the values in place, and
                 # a step after a sort that reads them through the sort's permutation
                 "in_place_bytes_per_parcel": 61.8, "perm_bytes_per_parcel": 70.8,
-                "source_sha256": "f8fbf0ab8f4cd842e4084a14b2f60d723dbdf678f39d3e21ed63c4ea784be0bc"}
+                "source_sha256": "fffcb314816be2b68175ad849141a8e82a6f623fda27dbcce6ae51f15dc37840"}
 
 
 def step_traffic(args, np_, start):
