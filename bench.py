@@ -214,8 +214,8 @@ STEP_TRAFFIC = {"workload": "dense", "precision": 32,
                 # DRAM bytes per parcel of one launch of each step-kernel instance, ncu on the
                 # 8M-parcel dense bed at step 150: a step that updates the values in place, and
                 # a step after a sort that reads them through the sort's permutation
-                "in_place_bytes_per_parcel": 61.8, "perm_bytes_per_parcel": 70.8,
-                "source_sha256": "fffcb314816be2b68175ad849141a8e82a6f623fda27dbcce6ae51f15dc37840"}
+                "in_place_bytes_per_parcel": 61.9, "perm_bytes_per_parcel": 70.8,
+                "source_sha256": "0ee6ad4b41e09ffab25f61c3c32641304a4f324bcd82ebf9c1f979a375e5ad0b"}
 
 
 def step_traffic(args, np_, start):

@@ -577,9 +577,11 @@ __device__ __forceinline__ int queue_offcell(T* wq, int n, unsigned pend, int ce
 }
 
 // Deposits the warp's npend queued records (all 32 lanes call it, npend uniform) and empties
-// the queue.
+// the queue. A call, not inlined: the cell kernel's parcel loop runs it rarely, and its code
+// inlined at each use made the loop's instructions miss in the instruction cache (the step
+// kernel took 6% longer).
 template <class T, int NV, bool EXACT = false>
-__device__ __forceinline__ void drain_offcell(const KParams<T>& p, u64* fx, int* kr, int i0, int j0,
+__device__ __noinline__ void drain_offcell(const KParams<T>& p, u64* fx, int* kr, int i0, int j0,
                                               int k0, CellBits cb, int q0, const T* wq, int npend) {
   constexpr int W = Words<T>::n;
   const int lane = threadIdx.x & 31, g = lane >> 3, corner = lane & 7;
@@ -1134,10 +1136,78 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
     if (PERM && lv + 1 < nmax) pf_src = perm_at(lv + 1, pf_off);
   };
   // the first level's loads are in flight while the node-field tile completes
-  if (PERM && nmax > 0) pf_src = perm_at(0, pf_off);
-  if (nmax > 0) load_level(0);
+  if (MODE != MODE_VOLUME && PERM && nmax > 0) pf_src = perm_at(0, pf_off);
+  if (MODE != MODE_VOLUME && nmax > 0) load_level(0);
   if (MODE != MODE_VOLUME) cp_async_wait<0>();
   __syncthreads();                               // the node-field tile is complete
+  if constexpr (MODE == MODE_VOLUME) {
+    // The volume deposit's work per level is short: one level of prefetch would leave the
+    // loads' latency (after a sort, the permutation's index and then the values) exposed at
+    // every level. Its loads are issued VG levels at a time: the group's indices, then its
+    // values; then the group's levels are processed in order, as the step's loop does.
+    constexpr int VG = 8;
+    int ld_off = off;                            // first position of the next level to load
+    for (int r0 = 0; r0 < nmax; r0 += VG) {
+      uint32_t gq[VG];
+      T gv[VG][5];                               // x y z d omega
+#pragma unroll
+      for (int u = 0; u < VG; ++u) {
+        const bool a = n > r0 + u;
+        const unsigned bl = __ballot_sync(FULL, a);
+        const int q = ld_off + __popc(bl & below);
+        gq[u] = a ? (PERM ? __ldg(src.perm + q) : (uint32_t)q) : 0u;
+        ld_off += __popc(bl);
+      }
+#pragma unroll
+      for (int u = 0; u < VG; ++u) {
+        const bool a = n > r0 + u;
+#pragma unroll
+        for (int f = 0; f < 5; ++f) gv[u][f] = a ? src.a[f < 3 ? f : f + 3][gq[u]] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < VG; ++u) {
+        const int r = r0 + u;
+        if (r >= nmax) break;                    // uniform over the warp
+        const bool act = n > r;
+        const unsigned bal = __ballot_sync(FULL, act);
+        if (r == sw) {           // the first cell is done: leave its sums, go on to the second
+          sums.template store<q0, q1>(cbuf, tid);
+          if (EXACT_V) vbuf[tid] = vtot;
+          sums.zero();
+          vtot = 0;
+          lc = lcB;
+          ci = bi0 + lc % BX; cj = bj0 + (lc / BX) % BY; ck = bk0 + lc / (BX * BY);
+        }
+        bool off_old = false;
+        int co = 0;
+        T xo[3] = {T(0), T(0), T(0)};
+        T V = T(0);
+        if (act) {
+          const T d = gv[u][3], om = gv[u][4];
+          Cell3<T> c;
+          const bool own = bin3_expect(p, gv[u][0], gv[u][1], gv[u][2], ci, cj, ck, c);
+          V = om * (d * d * d) * p.vcoef;
+          if (own) {
+            W8<T> Wq;
+            T yz[4];
+            corner_weights(c.xi, Wq, yz);
+            sums.add_vol(V, Wq);
+            if (EXACT_V) { u64 vf[W]; to_fixed(V, p.mV, vf, p.errs); vtot += (long long)vf[0]; }
+          } else {
+            off_old = true;
+            co = pack_cell(p, cb, c.i, c.j, c.k);
+            xo[0] = c.xi[0]; xo[1] = c.xi[1]; xo[2] = c.xi[2];
+          }
+        }
+        const unsigned po = __ballot_sync(FULL, off_old);
+        if (po) {
+          if (n_old + __popc(po) > QCAP) { drain_old(); n_old = 0; }
+          n_old = queue_offcell(q_old, n_old, po, co, xo[0], xo[1], xo[2], V, T(0), T(0), T(0));
+        }
+        off += __popc(bal);
+      }
+    }
+  } else {
   for (int r = 0; r < nmax; ++r) {
     T cv[8];
 #pragma unroll
@@ -1272,6 +1342,7 @@ k_cells(const __grid_constant__ KParams<T> p0, const KParams<T>* __restrict__ be
       }
     }
     off += __popc(bal);
+  }
   }
   if (n_old) drain_old();
   if (n_new) drain_new();
@@ -1620,13 +1691,16 @@ __global__ void k_count_bricks(const int* __restrict__ cstart, long long nbricks
 }
 
 // a10: deterministic reduction of the per-brick objective partials into (dP, H): OBJ_BLOCKS
-// blocks each sum a fixed slice of bricks with a fixed tree; the last block to finish sums
-// the slice partials in order. obj[0] = dP = sum f s_z / area, obj[1] = H = 2 sum V z / sum V.
+// blocks each sum a fixed slice of bricks with a fixed tree; the last block to finish loads
+// the slice partials at once and one thread sums them in order. obj[0] = dP = sum f s_z /
+// area, obj[1] = H = 2 sum V z / sum V.
 constexpr int OBJ_BLOCKS = 32, OBJ_THREADS = 256;
 __global__ void k_obj_reduce(const double* __restrict__ part, long long nb, double area,
                              double* __restrict__ slices, unsigned* __restrict__ count,
                              double* __restrict__ obj) {
+  static_assert(3 * OBJ_BLOCKS <= OBJ_THREADS, "one slice value per thread");
   __shared__ double s[3][OBJ_THREADS];
+  __shared__ double sl[3 * OBJ_BLOCKS];
   __shared__ bool last;
   const int t = threadIdx.x;
   const long long per = (nb + gridDim.x - 1) / gridDim.x;
@@ -1649,11 +1723,13 @@ __global__ void k_obj_reduce(const double* __restrict__ part, long long nb, doub
     last = atomicAdd(count, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && t == 0) {                          // every slice is written: sum them in order
-    __threadfence();
-    const volatile double* vs = slices;
+  if (!last) return;                             // uniform over the block
+  __threadfence();                               // every slice is written
+  if (t < 3 * (int)gridDim.x) sl[t] = __ldcg(slices + t);
+  __syncthreads();
+  if (t == 0) {                                  // in slice order
     double A = 0, B = 0, C = 0;
-    for (unsigned k = 0; k < gridDim.x; ++k) { A += vs[3 * k]; B += vs[3 * k + 1]; C += vs[3 * k + 2]; }
+    for (unsigned k = 0; k < gridDim.x; ++k) { A += sl[3 * k]; B += sl[3 * k + 1]; C += sl[3 * k + 2]; }
     obj[0] = A / area;
     obj[1] = C > 0 ? 2.0 * B / C : 0.0;
     *count = 0;                                  // ready for the next launch
