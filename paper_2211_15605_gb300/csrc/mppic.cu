@@ -47,6 +47,11 @@ struct mppic_handle {
   std::vector<const void*> gkey;
   cudaStream_t cap_stream = nullptr;             // capture stream (the caller's may be the legacy one)
   cudaStream_t stream = nullptr;
+  // side stream of a step call: the node pass runs there while a re-sort runs on `stream`,
+  // and each step's objective reduction while the next step's node pass and sort run.
+  // Forked and joined with events (no timing), so a captured call stays one graph.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_fin = nullptr, ev_red = nullptr;
   int device = 0;
   int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0;
   long long nnode = 0, nbricks = 0, nkeys = 0;
@@ -167,13 +172,14 @@ mppic_status fail(mppic_handle* h, mppic_status s, const char* fmt, ...) {
 
 inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Records a CUDA event pair around one phase on the handle's stream while profiling is
-// enabled, and counts the phase's kernel launches.
+// Records a CUDA event pair around one phase on the handle's stream (or the given one)
+// while profiling is enabled, and counts the phase's kernel launches.
 struct Phase {
   mppic_handle* h;
   int phase;
+  cudaStream_t st;
   size_t slot = (size_t)-1;
-  Phase(mppic_handle* h_, int ph) : h(h_), phase(ph) {
+  Phase(mppic_handle* h_, int ph, cudaStream_t s = nullptr) : h(h_), phase(ph), st(s ? s : h_->stream) {
     if (!h->prof) return;
     if (h->ev_used * 2 + 2 > h->ev.size()) {
       cudaEvent_t a, b;
@@ -185,7 +191,7 @@ struct Phase {
     }
     slot = h->ev_used++;
     h->ev_phase[slot] = ph;
-    cudaEventRecord(h->ev[2 * slot], h->stream);
+    cudaEventRecord(h->ev[2 * slot], st);
   }
   void launched(int n = 1) {
     if (!h->prof) return;
@@ -193,7 +199,7 @@ struct Phase {
     h->total_launches += n;
   }
   ~Phase() {
-    if (slot != (size_t)-1) cudaEventRecord(h->ev[2 * slot + 1], h->stream);
+    if (slot != (size_t)-1) cudaEventRecord(h->ev[2 * slot + 1], st);
   }
 };
 
@@ -481,22 +487,23 @@ mppic_status sort_into_scratch(mppic_handle* h, const mppic_parcels* pc, PArrays
 // Node pass over the layers deposited into (all layers if full), then roll the ranges.
 template <class T>
 mppic_status launch_finalize(mppic_handle* h, const KParams<T>& p, double* vs_out, bool full,
-                             const KParams<T>* beds = nullptr) {
-  Phase ph(h, PH_FINALIZE);
+                             const KParams<T>* beds = nullptr, cudaStream_t st = nullptr) {
+  if (!st) st = h->stream;
+  Phase ph(h, PH_FINALIZE, st);
   unsigned g = blocks(h->nnode, 256);
   if (g > 152u * 8u) g = 152u * 8u;
   if (beds) {                  // a batch: every node of every bed
     ph.launched(2);
-    k_finalize_b<T><<<g, 256, 0, h->stream>>>(beds, h->d_noff, h->nbeds, h->nnode);
+    k_finalize_b<T><<<g, 256, 0, st>>>(beds, h->d_noff, h->nbeds, h->nnode);
     LAUNCHED();
-    k_epoch_next<<<1, 1, 0, h->stream>>>(h->epoch);
+    k_epoch_next<<<1, 1, 0, st>>>(h->epoch);
     LAUNCHED();
     return MPPIC_OK;
   }
   ph.launched(2);
-  k_finalize<T><<<g, 256, 0, h->stream>>>(p, vs_out, full ? 1 : 0);
+  k_finalize<T><<<g, 256, 0, st>>>(p, vs_out, full ? 1 : 0);
   LAUNCHED();
-  k_range_roll<<<1, 1, 0, h->stream>>>(h->zr, h->epoch);
+  k_range_roll<<<1, 1, 0, st>>>(h->zr, h->epoch);
   LAUNCHED();
   return MPPIC_OK;
 }
@@ -731,9 +738,21 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
   const double area = h->cfg.nx * h->cfg.dx * h->cfg.ny * h->cfg.dy;
   const PArrays<T> copy = sorted_arrays<T>(h, false, false);
   bool in_copy = start_perm;                     // the values are (step 0: go) in the handle's copy
+  bool red_pending = false;                      // a reduction on the side stream not yet joined
   for (int it = 0; it < nsteps; ++it) {
     dst = in_copy ? copy : caller;
-    if (it > 0 && sort_due(h->step_counter + it)) {
+    // A step with a re-sort: the node pass of the last step's deposits (it reads the deposit
+    // accumulators and writes the node fields; the sort touches neither) runs on the side
+    // stream meanwhile, and the step kernel waits for both.
+    const bool sort_now = it > 0 && sort_due(h->step_counter + it);
+    if (sort_now) {
+      CU(cudaEventRecord(h->ev_fork, h->stream));
+      CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+      s = launch_finalize<T>(h, p, nullptr, false, beds, h->side);
+      if (s) return s;
+      CU(cudaEventRecord(h->ev_fin, h->side));
+    }
+    if (sort_now) {
       if (perm_sort) {
         s = sort_into_scratch<T>(h, pc, src, true, true, gas, true);   // keys from the previous step
         if (s) return s;
@@ -750,8 +769,12 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
       s = save_checkpoint<T>(h, it / h->ckpt_every, src, np);
       if (s) return s;
     }
-    s = launch_finalize<T>(h, p, nullptr, false, beds);
-    if (s) return s;
+    if (sort_now) {
+      CU(cudaStreamWaitEvent(h->stream, h->ev_fin, 0));
+    } else {
+      s = launch_finalize<T>(h, p, nullptr, false, beds);
+      if (s) return s;
+    }
     // implicit coupling (Sec. 2.2.2): the drag sums again at the head of every gas
     // iteration, each followed by the iteration's node update of the gas velocity
     for (int m = 0; m < h->cfg.coupling_iters; ++m) {
@@ -762,23 +785,33 @@ mppic_status step_impl(mppic_handle* h, mppic_parcels* pc, const mppic_gas* gas,
     }
     // the step before a sort in this call writes the sort keys of the new positions
     uint32_t* key_out = it + 1 < nsteps && sort_due(h->step_counter + it + 1) ? h->keys[0] : nullptr;
+    if (red_pending) {           // the step rewrites the per-brick objective partials
+      CU(cudaStreamWaitEvent(h->stream, h->ev_red, 0));
+      red_pending = false;
+    }
     s = launch_cells<T>(h, MODE_STEP, p, src, dst, (it == nsteps - 1 && !beds) ? pc->cell : nullptr, np,
                         beds, key_out);
     if (s) return s;
     src = dst;
-    {
-      Phase ph(h, PH_REDUCE);
+    {                            // the objectives on the side stream, while the next step's
+      CU(cudaEventRecord(h->ev_fork, h->stream));   // node pass and sort run
+      CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+      Phase ph(h, PH_REDUCE, h->side);
       ph.launched();
       if (beds)
-        k_obj_reduce_b<<<h->nbeds, 256, 0, h->stream>>>(
+        k_obj_reduce_b<<<h->nbeds, 256, 0, h->side>>>(
             h->obj_part, h->d_boff, h->d_area, obj_out ? obj_out + 2LL * it * h->nbeds : h->obj_tmp);
       else
-        k_obj_reduce<<<OBJ_BLOCKS, OBJ_THREADS, 0, h->stream>>>(
+        k_obj_reduce<<<OBJ_BLOCKS, OBJ_THREADS, 0, h->side>>>(
             h->obj_part, h->nbricks, area, h->obj_slices, h->obj_count,
             obj_out ? obj_out + 2 * it : h->obj_tmp);
       LAUNCHED();
     }
+    CU(cudaEventRecord(h->ev_red, h->side));
+    red_pending = true;
   }
+  if (red_pending) CU(cudaStreamWaitEvent(h->stream, h->ev_red, 0));   // joined: the call's
+                                                                         // work is on `stream`
   if (in_copy && np > 0)                         // the last step wrote the handle's copy
     for (int f = 0; f < 8; ++f)
       CU(cudaMemcpyAsync(caller.a[f], h->sorted[f], h->tsize * np, cudaMemcpyDeviceToDevice, h->stream));
@@ -1141,6 +1174,13 @@ mppic_status mppic_create(const mppic_config* cfg, int nbeds, const long long* b
     return true;
   };
   if (cudaGetDevice(&h->device) != cudaSuccess) s = fail(h, MPPIC_ERR_CUDA, "no CUDA device");
+  if (!s && (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventCreateWithFlags(&h->ev_fin, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventCreateWithFlags(&h->ev_red, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    s = fail(h, MPPIC_ERR_CUDA, "cannot create the side stream and its events");
+  }
   if (!s && cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
     s = fail(h, MPPIC_ERR_CUDA, "cannot read the SM count");
   if (!s && alloc((void**)&h->acc, sizeof(u64) * NQ * h->words * nnode) &&
@@ -1457,6 +1497,10 @@ void mppic_destroy(mppic_handle* h) {
   cudaFree(h->d_area); cudaFree(h->d_beds); cudaFree(h->wq);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_fin) cudaEventDestroy(h->ev_fin);
+  if (h->ev_red) cudaEventDestroy(h->ev_red);
   delete h;
 }
 
