@@ -204,7 +204,7 @@ def measured_peak():
 # FP64 operations per parcel of the FP64 step kernel (k_cells<double,1>): DADD + DMUL + 2 DFMA
 # thread instructions per parcel from the instruction counters of one ncu capture on the
 # 8M-parcel dense case: the work of the FP64 pipe, divisions and powers included.
-FP64_FLOPS_PER_PARCEL = 602
+FP64_FLOPS_PER_PARCEL = 617
 FP64_FLOPS_SOURCE = "ncu counters: (DADD + DMUL + 2 DFMA) / parcels of one launch, 8M-parcel dense bed"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32 step kernel per
