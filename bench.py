@@ -204,7 +204,7 @@ def measured_peak():
 # FP64 operations per parcel of the FP64 step kernel (k_cells<double,1>): DADD + DMUL + 2 DFMA
 # thread instructions per parcel from the instruction counters of one ncu capture on the
 # 8M-parcel dense case: the work of the FP64 pipe, divisions and powers included.
-FP64_FLOPS_PER_PARCEL = 617
+FP64_FLOPS_PER_PARCEL = 602
 FP64_FLOPS_SOURCE = "ncu counters: (DADD + DMUL + 2 DFMA) / parcels of one launch, 8M-parcel dense bed"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32 step kernel per
@@ -215,7 +215,7 @@ STEP_TRAFFIC = {"workload": "dense", "precision": 32,
                 # 8M-parcel dense bed at step 150: a step that updates the values in place, and
                 # a step after a sort that reads them through the sort's permutation
                 "in_place_bytes_per_parcel": 61.9, "perm_bytes_per_parcel": 70.8,
-                "source_sha256": "0ee6ad4b41e09ffab25f61c3c32641304a4f324bcd82ebf9c1f979a375e5ad0b"}
+                "source_sha256": "8d85d2eaf957585b9d998d4899a533cf145d4bcc2fe812bc11193a05a2633985"}
 
 
 def step_traffic(args, np_, start):
