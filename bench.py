@@ -215,7 +215,7 @@ STEP_TRAFFIC = {"workload": "dense", "precision": 32,
                 # 8M-parcel dense bed at step 150: a step that updates the values in place, and
                 # a step after a sort that reads them through the sort's permutation
                 "in_place_bytes_per_parcel": 61.9, "perm_bytes_per_parcel": 70.8,
-                "source_sha256": "8d85d2eaf957585b9d998d4899a533cf145d4bcc2fe812bc11193a05a2633985"}
+                "source_sha256": "6a46ab409e1b245d058fe8ad935e3c46650bde69f439a3f8ffdd2ac5cb2579a5"}
 
 
 def step_traffic(args, np_, start):

@@ -165,7 +165,7 @@ __device__ __forceinline__ bool xi_in_cell(float x, double, float inv_f, float i
 // formula gives the same index and in-cell coordinate). Returns whether the cell is (i, j, k).
 // FP64 form: the formula on all three axes once a test fails. Re-binning only the failing
 // axes, the compiler computed the formula's FP64 products for every parcel and selected
-// (12 more FP64 multiplies per parcel on the narrow FP64 pipe: the FP64 step 4% slower).
+// (12 more FP64 multiplies per parcel on the narrow FP64 pipe: the FP64 step 3% slower).
 template <class T>
 __device__ __forceinline__ bool bin3_expect(const KParams<T>& p, T x, T y, T z, int i, int j, int k,
                                             Cell3<T>& c) {
